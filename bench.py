@@ -1,0 +1,334 @@
+#!/usr/bin/env python3
+"""Benchmark: RandNet-Parareal time-to-solution on GB300.
+
+One *step* is one full solve (Alg. 1: k = 0 coarse sweep, then iterations
+of the parallel fine step, dataset append + features, exact leftmost slice,
+sequential RandNet predictor-corrector sweep and the Eq. 5 stopping rule)
+of the 2D diffusion-reaction workload: 128 x 128 x 2 periodic grid
+(d = 32768), N = 64 slices on [0, 5], F = RK4 2000 steps/slice, G = forward
+Euler 8 steps/slice, M = 100 ReLU features, m = 4 neighbours, lambda = 1e-7,
+tol = 1e-6, initial state i.i.d. N(0,1) (seeded, synthetic).  The timed
+form is the mixed-precision fused path (FP32 stencils, FP64 correction,
+ridge and norm); the plain FP64 GPU form is timed beside it.
+
+value = fine cell-updates per second over the whole job (sum over ranks of
+the fine RK4 unknown-steps the solves performed / max over ranks of the
+timed wall time).  ms_per_step = time-to-solution of one solve.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun every rank solves its own seeded replica (weak scaling, no
+collective on the data path); only the barrier and the max-reduction of the
+timings cross ranks.  ``--impl reference`` times the FP64 CPU oracle on the
+host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+WORKLOAD = "diffreact2d"
+METRIC = ("Parareal time-to-solution @tol 1e-6 vs plain FP64; cell-updates/s, %HBM; "
+          "p50/p99")
+UNIT = "cell-updates/s"
+
+# Algorithmic FP32 flops per fine cell-update (one unknown, one RK4 step) of
+# the diffusion-reaction stencil, counted from the formulas with every
+# multiply and add separate: per grid point and stage 16 (u) + 12 (v); per
+# unknown and step 13 for the stage combinations.
+FLOPS_PER_CELL_UPDATE = {"diffreact2d": (4 * (16 + 12) + 2 * 13) / 2.0}
+
+
+def peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return json.load(open(path))
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0,
+            "fallback": True}
+
+
+def fp32_alu_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
+    # 128 FP32 lanes per SM, an FMA counted as 2 flops
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"rnp_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(seconds_hint: float = 20.0) -> dict:
+    """The FP64 oracle on the host cores: a bounded sample of the same
+    workload (same grid, slices and coarse solver; nF cut to 40 of 2000
+    fine steps per slice), reported in fine cell-updates per second."""
+    import oracle
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    cfg = W.config(WORKLOAD, nF=40)
+    p = oracle.problem(cfg)
+    u0 = W.initial_condition(cfg)[0]
+    t0 = time.perf_counter()
+    rc, U, st, _ = oracle.solve(p, u0)
+    dt = time.perf_counter() - t0
+    return {"value": st.fine_cell_updates / dt, "unit": UNIT, "cores": cores,
+            "kind": "oracle",
+            "sample": (f"{WORKLOAD} 128x128x2, N=64, nF=40 of 2000 RK4 steps per slice, "
+                       f"full solve K={st.K} in {dt:.2f} s, FP64, slice-parallel over "
+                       f"{cores} threads")}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    samples = []
+    base = None
+    for i in range(args.warmup + args.steps):
+        b = cpu_baseline()
+        if i >= args.warmup:
+            samples.append(b["value"])
+        base = b
+    value = statistics.median(samples) if samples else base["value"]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD} (CPU sample, nF=40)", "grid": "128x128x2",
+                   "N": 64, "nF": 40, "nG": 8},
+        "cpu_baseline": {"kind": "oracle", "cores": base["cores"], "sample": base["sample"],
+                         "value": value, "unit": UNIT},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    import paper_2411_06225_gb300 as rnp
+    ws, rank, local = dist_env()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rnp.lib()
+    cfg = W.config(WORKLOAD, seed=W.CONFIGS[WORKLOAD]["seed"] + 1000 * rank)
+    d = W.dim(cfg)
+    N = cfg["N"]
+    u0_h = torch.as_tensor(W.initial_condition(cfg)).pin_memory()
+    u0 = u0_h.to(dev)
+    stream = torch.cuda.current_stream(dev)
+    prob = rnp.problem(cfg, precision=args.precision, exec="fused")
+    solver = rnp.Solver(prob, stream=stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
+
+    for _ in range(args.warmup):
+        solver.solve(u0)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_id = local
+    clocks = ClockSampler(gpu_id)
+    tts, fine_ms, cells, launches, stats = [], [], 0, 0, None
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1.0)                       # L2 flush between timed steps (untimed)
+        ev0.record(stream)
+        U, st = solver.solve(u0)
+        ev1.record(stream)
+        ev1.synchronize()
+        tts.append(ev0.elapsed_time(ev1))
+        fine_ms.append(st["t_fine_ms"] / max(st["K"], 1))
+        cells += st["fine_cell_updates"]
+        launches += st["kernel_launches"]
+        stats = st
+    barrier()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    t_sum = sum(tts) / 1e3
+    # max over ranks of the timed device time, sum of the work
+    t_max, cells_all = t_sum, cells
+    if dist is not None:
+        tt = torch.tensor([t_sum], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        cc = torch.tensor([float(cells)], device=dev, dtype=torch.float64)
+        dist.all_reduce(cc, op=dist.ReduceOp.SUM)
+        t_max, cells_all = tt.item(), cc.item()
+    value = cells_all / t_max
+
+    # e2e: host buffers in, result back to host, through the same C ABI
+    U_h = torch.empty((1, N + 1, d), dtype=torch.float64).pin_memory()
+    e2e_t = []
+    for _ in range(max(2, min(args.steps, 3))):
+        flush.fill_(1.0)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        u0_d = u0_h.to(dev, non_blocking=True)
+        Ud, st_e = solver.solve(u0_d)
+        U_h.copy_(Ud, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_value = st_e["fine_cell_updates"] * ws / max(e2e_t) if ws > 1 else \
+        st_e["fine_cell_updates"] / statistics.median(e2e_t)
+
+    extra = {}
+    if rank == 0 and not args.skip_fp64:
+        # plain FP64 GPU RandNet-Parareal (per-stage kernels, FP64 features)
+        for label, prec, ex in (("fp64_plain", "fp64", "plain"), ("fp64_fused", "fp64", "fused")):
+            with rnp.Solver(rnp.problem(cfg, precision=prec, exec=ex), stream=stream) as s2:
+                torch.cuda.synchronize(dev)
+                ev0.record(stream)
+                U2, st2 = s2.solve(u0)
+                ev1.record(stream)
+                ev1.synchronize()
+                extra[f"tts_{label}_ms"] = ev0.elapsed_time(ev1)
+                extra[f"K_{label}"] = st2["K"]
+                if label == "fp64_fused":
+                    extra["mixed_vs_fp64_max_abs"] = float((U - U2).abs().max().item())
+                    extra["mixed_vs_fp64_rel"] = float(((U - U2).abs().max() /
+                                                        U2.abs().max()).item())
+
+    if rank == 0:
+        pk = peaks()
+        sm_mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+        flops_cu = FLOPS_PER_CELL_UPDATE[WORKLOAD]
+        cells_per_launch = stats["fine_cell_updates"] / max(stats["K"], 1)
+        achieved = cells_per_launch * flops_cu / (statistics.mean(fine_ms) / 1e3) / 1e12
+        peak_alu = fp32_alu_peak_tflops(pk.get("sm_max_mhz", 2070.0))
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": statistics.mean(tts), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD} 128x128x2 periodic, N=64, F=RK4x2000, "
+                                   "G=Eulerx8, M=100, m=4, tol=1e-6",
+                       "precision": args.precision, "exec": "fused",
+                       "replica_per_rank": True, "l2": "flushed between timed steps "
+                       "(256 MB write)", "parallelism": f"replicas x{ws}"},
+            "time_to_solution_ms": {"p50": statistics.median(tts), "min": min(tts),
+                                    "max": max(tts)},
+            "K": stats["K"], "fine_ms_per_iteration": statistics.mean(fine_ms),
+            "sweep_ms": stats["t_sweep_ms"], "fit_ms": stats["t_fit_ms"],
+            "roofline": {"kernel": "k_stencil_fused<DIFFREACT,float>", "bound": "alu",
+                         "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
+                         "frac": achieved / peak_alu, "traffic": None,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock "
+                                        f"{pk.get('sm_max_mhz', 2070.0)} MHz (MEASURED_PEAKS)"},
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": int(u0_h.numel() * 8),
+                    "d2h_bytes_per_step": int(U_h.numel() * 8),
+                    "ms_per_step": statistics.median(e2e_t) * 1e3},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "wall_s": t_wall,
+        }
+        line.update(extra)
+        if not args.skip_cpu:
+            try:
+                line["cpu_baseline"] = cpu_baseline()
+            except Exception as e:  # report, do not fail the GPU line
+                line["cpu_baseline"] = {"error": repr(e)}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    solver.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

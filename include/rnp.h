@@ -1,0 +1,209 @@
+/*
+ * rnp.h -- C ABI of librnp, a GB300 (sm_103a) implementation of the
+ * data-parallel hot path of RandNet-Parareal (Gattiglio, Grigoryeva,
+ * Tamborrino, "RandNet-Parareal: a time-parallel PDE solver using Random
+ * Neural Networks", NeurIPS 2024).
+ *
+ * The library solves the initial value problem of Eq. 1,
+ *     du/dt = h(u),  t in [t0, tN],  u(t0) = u0,  u in R^d,
+ * split into N time slices (Sec. 2), with a cheap coarse propagator G
+ * (forward Euler or RK4), an accurate fine propagator F (classic RK4) and
+ * the RandNet correction of Eq. randnet: a fixed random hidden layer
+ * (Eq. HA, weights and biases U(-1,1), ReLU) whose linear readout is a
+ * ridge fit (Eq. ridgeless) on the m nearest stored pairs (App. B), inside
+ * the predictor-corrector sweep of Eq. 3 and the loop of Alg. 1.
+ *
+ * Conventions shared by every call
+ *   - Array arguments are caller-owned DEVICE pointers to contiguous FP64
+ *     data on the device that was current at rnp_create.  The library never
+ *     frees them and never keeps them past the call.
+ *   - d = ncomp * nx * ny * nz unknowns per state, component-major, then z,
+ *     then y, then x (x fastest).  ncomp: Burgers/heat/advection 1,
+ *     diffusion-reaction and Brusselator 2 (u then v), shallow water 3
+ *     (h, hu, hv).
+ *   - B = problem.batch independent initial conditions share the grid,
+ *     N, F, G and the random weights; each has its own dataset, scaling and
+ *     convergence state.  Batched arrays put the member index outermost.
+ *   - Calls enqueue work on the stream given to rnp_create and return
+ *     without waiting, except rnp_solve (which returns statistics) and
+ *     rnp_coarse_sweep / rnp_randnet_predict (which read the dataset size on
+ *     the host).  Inputs must be ready on that stream.
+ *   - A context is not thread-safe; use one per concurrent solve.
+ *   - No call throws.  Every call returns an rnp_status; on failure
+ *     rnp_last_error(ctx) holds a message until the next call on ctx.
+ *   - A context owns its device memory (slice states, the dataset arena of
+ *     scaled inputs, targets and features, the random weights, workspace),
+ *     allocated at rnp_create and released by rnp_destroy.
+ */
+#ifndef RNP_H
+#define RNP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rnp_ctx rnp_ctx;
+
+typedef enum {
+  RNP_OK = 0,
+  RNP_EINVAL = 1,      /* bad argument or unsupported configuration        */
+  RNP_ENOMEM = 2,      /* device allocation failed or dataset arena full   */
+  RNP_ECUDA = 3,       /* a CUDA runtime call failed                        */
+  RNP_ENONFINITE = 4,  /* a state became NaN/Inf, or the ridge solve failed */
+  RNP_ENOTCONV = 5,    /* max_iters reached before Eq. 5 held for all i     */
+  RNP_ETIMEOUT = 6,    /* a bounded device wait gave up                     */
+  RNP_EBUSY = 7        /* the server has no free slot                       */
+} rnp_status;
+
+/* h(u) of Eq. 1: periodic finite-difference semi-discretisations of the
+ * paper's test systems (Sec. 5.1 Burgers, Sec. 5.2 diffusion-reaction,
+ * App. E Brusselator, Sec. 5.3 shallow water) and two linear operators. */
+typedef enum {
+  RNP_BURGERS1D = 0,   /* param: nu                                        */
+  RNP_DIFFREACT2D = 1, /* param: Du, Dv, c   (FitzHugh-Nagumo kinetics)   */
+  RNP_BRUSS2D = 2,     /* param: a, b, D0, D1                              */
+  RNP_BRUSS3D = 3,     /* param: a, b, D0, D1                              */
+  RNP_SWE2D = 4,       /* param: g  (Rusanov flux, flat bottom)            */
+  RNP_HEAT = 5,        /* param: D  (1, 2 or 3 dimensions)                 */
+  RNP_ADVECT1D = 6     /* param: c                                         */
+} rnp_pde;
+
+typedef enum { RNP_FP64 = 0, RNP_MIXED = 1 } rnp_precision;
+/* FP64: every step in double precision; F and G are bit-identical to a
+ *       plain serial FP64 evaluation of the same formulas.
+ * MIXED: F and G stencils in FP32 arithmetic, random features from BF16
+ *       operands with FP32 accumulation, neighbour search screened in FP32
+ *       and decided in FP64, ridge solve, correction and norm in FP64.   */
+
+typedef enum { RNP_EXEC_FUSED = 0, RNP_EXEC_PLAIN = 1 } rnp_exec;
+/* FUSED: one launch advances every active slice through all of its steps,
+ *        each slice resident in the shared memory of a thread-block cluster.
+ * PLAIN: one launch per Runge-Kutta stage over global memory (baseline). */
+
+typedef enum { RNP_CORR_RANDNET = 0, RNP_CORR_PARAREAL = 1 } rnp_corr;
+/* RANDNET: f_hat of Eq. randnet.  PARAREAL: f_hat of Eq. 4. */
+
+typedef enum { RNP_SCALE_MINMAX = 0, RNP_SCALE_NONE = 1 } rnp_scale;
+/* MINMAX: the RandNet input is rescaled per species to [-1,1] from the
+ * k = 0 coarse trajectory (Alg. 1 initialisation, Alg. 3).  NONE: identity. */
+
+typedef enum { RNP_G_EULER = 0, RNP_G_RK4 = 1 } rnp_gscheme;
+
+#define RNP_MAX_BATCH 64
+#define RNP_MAX_M 32   /* largest number of nearest neighbours m */
+
+typedef struct {
+  int pde;                /* rnp_pde                                        */
+  int nx, ny, nz;         /* grid points per axis (1 for unused axes)       */
+  double lx, ly, lz;      /* periodic domain lengths                        */
+  double param[8];        /* PDE coefficients (see rnp_pde)                 */
+  double t0, tN;          /* time interval of Eq. 1                         */
+  int N;                  /* time slices (Sec. 2)                           */
+  int nF, nG;             /* steps of F (RK4) and G per slice               */
+  int M, m;               /* hidden neurons (Eq. HA), neighbours (App. B)   */
+  double lambda;          /* ridge penalty of Eq. ridgeless (> 0)           */
+  uint64_t seed;          /* seed of A and zeta (Alg. 3)                    */
+  double tol;             /* epsilon of Eq. 5                               */
+  int max_iters;          /* iteration cap, 1 <= max_iters <= N             */
+  int corr;               /* rnp_corr                                       */
+  int scale_mode;         /* rnp_scale                                      */
+  int gscheme;            /* rnp_gscheme                                    */
+  int precision;          /* rnp_precision                                  */
+  int exec;               /* rnp_exec                                       */
+  int batch;              /* independent initial conditions, 1..64          */
+  int cluster;            /* fused stencil: CTAs per slice (0 = auto)       */
+  int threads;            /* fused stencil: threads per CTA (0 = auto)      */
+  long long max_pairs;    /* dataset rows per member (0 = enough for
+                             max_iters iterations)                          */
+} rnp_problem;
+
+typedef struct {
+  int K;                  /* iterations performed (max over the batch)      */
+  int L;                  /* min over the batch of the last converged index */
+  int converged;          /* every member reached L = N                     */
+  long long pairs;        /* dataset rows over the batch                    */
+  long long fine_cell_updates; /* sum over F runs of nF * d                */
+  int lambda_escalations; /* ridge retries with lambda x 10                 */
+  double t_fine_ms;       /* device time in F (events on the ctx stream)    */
+  double t_sweep_ms;      /* device time in the sequential sweeps           */
+  double t_fit_ms;        /* device time appending pairs and features       */
+  double t_total_ms;      /* wall time of the call                          */
+  int K_each[RNP_MAX_BATCH];  /* per-member iterations                      */
+} rnp_stats;
+
+/* Create a context for one problem.  cuda_stream is a cudaStream_t (NULL
+ * for the legacy default stream).  Allocates every device buffer the solve
+ * needs (dataset arena sized for max_iters iterations: at most
+ * N - k + 1 pairs are added at iteration k, Alg. 1 with Eq. 6).
+ * Errors: RNP_EINVAL (bad sizes or parameters), RNP_ENOMEM, RNP_ECUDA.   */
+rnp_status rnp_create(const rnp_problem* prob, void* cuda_stream, rnp_ctx** out);
+
+/* Release every resource of ctx (NULL is allowed).  Waits for the stream. */
+rnp_status rnp_destroy(rnp_ctx* ctx);
+
+/* Fine propagator F on n slice starts per member (Sec. 2: F run "in
+ * parallel" across slices; Alg. 1, parallel step).
+ *   U_in  : device [B][n][d]  slice start states
+ *   U_out : device [B][n][d]  F(U_in); may not alias U_in
+ * 1 <= n <= N.  Enqueues one launch.                                      */
+rnp_status rnp_fine_batch(rnp_ctx* ctx, const double* U_in, int n, double* U_out);
+
+/* Sequential predictor-corrector sweep, Eq. 3 with the context's f_hat:
+ *   U[b][first] = U_first[b];
+ *   U[b][i] = G(U[b][i-1]) + f_hat(U[b][i-1]),  i = first+1 .. N.
+ *   U_first : device [B][d];  U : device [B][N+1][d].
+ * With an empty dataset f_hat = 0 (the k = 0 coarse sweep of Alg. 1); such
+ * a sweep from first = 0 also sets the scaling of Alg. 1 from U[b][0..N]
+ * when scale_mode is MINMAX.  0 <= first <= N.                            */
+rnp_status rnp_coarse_sweep(rnp_ctx* ctx, int first, const double* U_first,
+                            double* U);
+
+/* Append P training pairs per member to the dataset D_k of Eq. 6: inputs
+ * Uin (unscaled) and targets Y = (F - G)(Uin).  The context stores the
+ * scaled input, the target and its random features phi = ReLU(A s + zeta)
+ * (Eq. HA); the readout itself is refit per query, on the m nearest pairs,
+ * inside rnp_randnet_predict (Alg. 3).
+ *   Uin, Y : device [B][P][d].  Errors: RNP_ENOMEM when the arena is full.*/
+rnp_status rnp_randnet_fit(rnp_ctx* ctx, const double* Uin, const double* Y, int P);
+
+/* RandNet correction of Eq. randnet for one query per member:
+ * out[b] = W_hat^T ReLU(A s(q[b]) + zeta), W_hat the ridge readout of
+ * Eq. ridgeless fit on the m nearest stored pairs of q[b] (App. B), solved
+ * in its dual m x m form.  A member with no stored pair gets 0.
+ *   q, out : device [B][d].                                               */
+rnp_status rnp_randnet_predict(rnp_ctx* ctx, const double* q, double* out);
+
+/* Full RandNet-Parareal solve (Alg. 1 with Eq. 3, Eq. 5, Eq. randnet or
+ * Eq. 4).  Resets the dataset and scaling, then iterates until every state
+ * passed Eq. 5 or max_iters.
+ *   u0 : device [B][d];  U : device [B][N+1][d] receives U_0 .. U_N.
+ *   stats : host, may be NULL.
+ * Returns RNP_OK, or RNP_ENOTCONV with U holding the last iterate.
+ * Blocks until the result is on the device.                               */
+rnp_status rnp_solve(rnp_ctx* ctx, const double* u0, double* U, rnp_stats* stats);
+
+/* Message of the last failed call on ctx ("" if none).  ctx may be NULL
+ * for errors raised by rnp_create. */
+const char* rnp_last_error(const rnp_ctx* ctx);
+
+/* --- inspection helpers (not steps of the method) ----------------------- */
+
+/* Copy the random weights of Alg. 3 to device buffers A [M][d], zeta [M]. */
+rnp_status rnp_get_weights(rnp_ctx* ctx, double* A, double* zeta);
+/* Set (host in) or read (host out) the per-member affine scaling:
+ * c, r : host [B][3]; s(u) = (u - c[species]) / r[species].               */
+rnp_status rnp_set_scaling(rnp_ctx* ctx, const double* c, const double* r);
+rnp_status rnp_get_scaling(rnp_ctx* ctx, double* c, double* r);
+/* Drop every stored pair and the scaling. */
+rnp_status rnp_reset(rnp_ctx* ctx);
+/* Host out: pairs [B] currently stored. */
+rnp_status rnp_get_pairs(rnp_ctx* ctx, long long* pairs);
+/* Unknowns per state. */
+long long rnp_dim(const rnp_problem* prob);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,739 @@
+// api.cu -- the C ABI of librnp (include/rnp.h) and the host orchestration
+// of Alg. 1: the k = 0 coarse sweep, then per iteration the parallel fine
+// step, the dataset append of Eq. 6, the exact leftmost slice, the
+// sequential predictor-corrector sweep of Eq. 3 and the stopping rule of
+// Eq. 5.  All arithmetic runs in the kernels of stencil.cu and randnet.cu;
+// the host only builds work lists and reads back one norm vector per
+// iteration.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "rnp_internal.h"
+
+using namespace rnp;
+
+struct rnp_ctx {
+  rnp_problem p;
+  Geom g;
+  Coef coef;
+  int dev = 0;
+  cudaStream_t st = nullptr;
+  int B = 1, N = 1, M = 1, m = 1;
+  long long d = 0, cap = 0;
+  bool fp32 = false, plain = false, randnet = true;
+  StencilCfg cfgF{}, cfgG{};
+  double dtF = 0, dtG = 0;
+  int schemeG = SCHEME_EULER;
+
+  // device state
+  double *U = nullptr, *Fv = nullptr, *Gc = nullptr, *Yv = nullptr, *gbuf = nullptr,
+         *qbuf = nullptr, *phic = nullptr, *phiq = nullptr;
+  double *Sds = nullptr, *Yds = nullptr, *Phi = nullptr;
+  double *A = nullptr, *zeta = nullptr;
+  double *sc = nullptr, *sr = nullptr, *scale_work = nullptr;
+  double *feat_part = nullptr, *nn_part = nullptr, *dist = nullptr, *alpha = nullptr;
+  int *idx = nullptr, *meff = nullptr, *flags = nullptr;  // flags: esc, fail, nonfinite
+  int* dP = nullptr;
+  unsigned long long* err = nullptr;
+  double* plain_work = nullptr;
+  long long* d_items = nullptr;   // src, dst, soff, phioff tables (4 * itemcap)
+  int* d_app = nullptr;           // b, j, p (3 * itemcap)
+  int* d_gate = nullptr;          // (N + 1) * B
+  int itemcap = 0;
+  int feat_rows_cap = 0;
+
+  // host mirrors
+  long long* h_items = nullptr;   // pinned
+  int* h_app = nullptr;           // pinned
+  int* h_gate = nullptr;          // pinned
+  unsigned long long* h_err = nullptr;  // pinned (B * (N+1))
+  int* h_flags = nullptr;         // pinned (4)
+  std::vector<int> P;             // pairs per member
+  bool weights_ready = false, scaling_ready = false;
+  double h_c[RNP_MAX_BATCH * 3], h_r[RNP_MAX_BATCH * 3];
+
+  cudaEvent_t ev[6] = {};
+  std::string msg;
+};
+
+static thread_local std::string g_create_error;
+
+namespace {
+
+struct DevGuard {
+  int prev = -1;
+  explicit DevGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DevGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+rnp_status fail(rnp_ctx* c, rnp_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->msg = buf; else g_create_error = buf;
+  return s;
+}
+
+#define CK(call)                                                                   \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      return fail(c, RNP_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                  __FILE__, __LINE__);                                             \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  if (count == 0) { *p = nullptr; return cudaSuccess; }
+  return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+const char* validate(const rnp_problem* p) {
+  if (!p) return "problem is NULL";
+  if (p->pde < RNP_BURGERS1D || p->pde > RNP_ADVECT1D) return "unknown pde";
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return "grid sizes must be >= 1";
+  if ((p->pde == RNP_BURGERS1D || p->pde == RNP_ADVECT1D) && (p->ny != 1 || p->nz != 1))
+    return "1D problems need ny = nz = 1";
+  if ((p->pde == RNP_DIFFREACT2D || p->pde == RNP_BRUSS2D || p->pde == RNP_SWE2D) && p->nz != 1)
+    return "2D problems need nz = 1";
+  if (p->pde == RNP_HEAT && p->nz > 1 && p->ny < 2) return "3D heat needs ny > 1";
+  if (p->nx < 3 || (p->ny > 1 && p->ny < 3) || (p->nz > 1 && p->nz < 3))
+    return "every used axis needs >= 3 points";
+  if (!(p->lx > 0) || !(p->ly > 0) || !(p->lz > 0)) return "domain lengths must be > 0";
+  if (!(p->tN > p->t0)) return "tN must exceed t0";
+  if (p->N < 1) return "N must be >= 1";
+  if (p->nF < 1 || p->nG < 1) return "nF and nG must be >= 1";
+  if (p->M < 1 || p->M > 4096) return "M must be in [1, 4096]";
+  if (p->m < 1 || p->m > RNP_MAX_M) return "m must be in [1, 32]";
+  if (!(p->lambda >= 0)) return "lambda must be >= 0";
+  if (!(p->tol >= 0)) return "tol must be >= 0";
+  if (p->max_iters < 1) return "max_iters must be >= 1";
+  if (p->batch < 1 || p->batch > RNP_MAX_BATCH) return "batch must be in [1, 64]";
+  if (p->corr != RNP_CORR_RANDNET && p->corr != RNP_CORR_PARAREAL) return "unknown corr";
+  if (p->scale_mode != RNP_SCALE_MINMAX && p->scale_mode != RNP_SCALE_NONE)
+    return "unknown scale_mode";
+  if (p->gscheme != RNP_G_EULER && p->gscheme != RNP_G_RK4) return "unknown gscheme";
+  if (p->precision != RNP_FP64 && p->precision != RNP_MIXED) return "unknown precision";
+  if (p->exec != RNP_EXEC_FUSED && p->exec != RNP_EXEC_PLAIN) return "unknown exec";
+  if (p->cluster < 0 || p->cluster > 16 || p->threads < 0 || p->threads > 512 ||
+      p->threads % 32)
+    return "cluster must be in [0,16] and threads a multiple of 32 in [0,512]";
+  if (p->max_pairs < 0) return "max_pairs must be >= 0";
+  return nullptr;
+}
+
+void destroy_buffers(rnp_ctx* c) {
+  void* bufs[] = {c->U, c->Fv, c->Gc, c->Yv, c->gbuf, c->qbuf, c->phic, c->phiq, c->Sds,
+                  c->Yds, c->Phi, c->A, c->zeta, c->sc, c->sr, c->scale_work, c->feat_part,
+                  c->nn_part, c->dist, c->alpha, c->idx, c->meff, c->flags, c->dP, c->err,
+                  c->plain_work, c->d_items, c->d_app, c->d_gate};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (c->h_items) cudaFreeHost(c->h_items);
+  if (c->h_app) cudaFreeHost(c->h_app);
+  if (c->h_gate) cudaFreeHost(c->h_gate);
+  if (c->h_err) cudaFreeHost(c->h_err);
+  if (c->h_flags) cudaFreeHost(c->h_flags);
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+}
+
+// ---------------------------------------------------------------------------
+// Building blocks
+// ---------------------------------------------------------------------------
+rnp_status run_stencil(rnp_ctx* c, bool fine, const double* in, double* out, double* out2,
+                       const Items& it) {
+  const int scheme = fine ? SCHEME_RK4 : c->schemeG;
+  const int steps = fine ? c->p.nF : c->p.nG;
+  const double dt = fine ? c->dtF : c->dtG;
+  cudaError_t e;
+  if (c->plain)
+    e = launch_stencil_plain(c->g, c->coef, scheme, steps, dt, in, out, out2, it,
+                             c->plain_work, c->st);
+  else
+    e = launch_stencil_fused(c->g, c->coef, c->fp32, scheme, steps, dt, in, out, out2, it,
+                             fine ? c->cfgF : c->cfgG, c->st);
+  if (e != cudaSuccess)
+    return fail(c, RNP_ECUDA, "stencil launch failed: %s", cudaGetErrorString(e));
+  return RNP_OK;
+}
+
+Items affine(int n, long long sb, long long ss, long long db, long long ds, const int* gate) {
+  Items it{};
+  it.src_off = nullptr; it.src_base = sb; it.src_stride = ss;
+  it.dst_off = nullptr; it.dst_base = db; it.dst_stride = ds;
+  it.dst2_off = nullptr; it.dst2_base = 0; it.dst2_stride = 0;
+  it.gate = gate;
+  it.n = n;
+  return it;
+}
+
+rnp_status ensure_weights(rnp_ctx* c) {
+  if (c->weights_ready) return RNP_OK;
+  CK(launch_weights(c->p.seed, c->M, c->d, c->A, c->zeta, nullptr, nullptr, nullptr, c->st));
+  c->weights_ready = true;
+  return RNP_OK;
+}
+
+rnp_status upload_P(rnp_ctx* c) {
+  // small synchronous copy from a pinned staging word block
+  for (int b = 0; b < c->B; ++b) c->h_flags[4 + b] = c->P[b];
+  CK(cudaMemcpyAsync(c->dP, c->h_flags + 4, sizeof(int) * c->B, cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return RNP_OK;
+}
+
+int Pmax(const rnp_ctx* c) {
+  int x = 0;
+  for (int b = 0; b < c->B; ++b) x = std::max(x, c->P[b]);
+  return x;
+}
+
+// RandNet prediction for one query per member: the scaled query is written to
+// qbuf, its features to phi_dst (member stride phi_bstride); alpha / idx /
+// meff are left on the device for the update kernel.
+rnp_status predict_core(rnp_ctx* c, const double* q, long long q_base, long long q_bstride,
+                        double* phi_dst, long long phi_base, long long phi_bstride,
+                        const int* gate) {
+  Rows src{nullptr, q_base, q_bstride};
+  Rows qrows{nullptr, 0, c->d};
+  CK(launch_scale_rows(c->g, q, src, nullptr, 1, c->sc, c->sr, c->qbuf, qrows, c->B, gate, c->st));
+  Rows prow{nullptr, phi_base, phi_bstride};
+  CK(launch_features64(c->A, c->zeta, c->M, c->d, c->qbuf, qrows, c->B, phi_dst, prow,
+                       c->feat_part, gate, c->st));
+  const int pm = Pmax(c);
+  CK(launch_nn_partial(c->qbuf, c->Sds, c->cap, c->d, c->dP, pm, c->B, c->nn_part, gate, c->st));
+  CK(launch_topm_ridge(c->nn_part, nn_chunks(c->d), c->Phi, c->cap, c->M, phi_dst + phi_base,
+                       phi_bstride, c->dP, pm, c->B, c->m, c->p.lambda, c->dist, c->alpha,
+                       c->idx, c->meff, c->flags + 0, c->flags + 1, gate, c->st));
+  return RNP_OK;
+}
+
+rnp_status read_flags(rnp_ctx* c, int* esc, int* failf, int* nonfinite) {
+  CK(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  *esc = c->h_flags[0];
+  *failf = c->h_flags[1];
+  *nonfinite = c->h_flags[2];
+  return RNP_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+long long rnp_dim(const rnp_problem* p) {
+  if (!p) return 0;
+  const int nc = (p->pde == RNP_SWE2D) ? 3
+                 : (p->pde == RNP_DIFFREACT2D || p->pde == RNP_BRUSS2D || p->pde == RNP_BRUSS3D)
+                     ? 2
+                     : 1;
+  return (long long)nc * p->nx * p->ny * p->nz;
+}
+
+const char* rnp_last_error(const rnp_ctx* ctx) {
+  return ctx ? ctx->msg.c_str() : g_create_error.c_str();
+}
+
+rnp_status rnp_create(const rnp_problem* prob, void* cuda_stream, rnp_ctx** out) {
+  rnp_ctx* c = nullptr;
+  if (!out) return fail(nullptr, RNP_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (const char* why = validate(prob)) return fail(nullptr, RNP_EINVAL, "%s", why);
+  c = new (std::nothrow) rnp_ctx();
+  if (!c) return fail(nullptr, RNP_ENOMEM, "host allocation failed");
+  c->p = *prob;
+  if (cudaGetDevice(&c->dev) != cudaSuccess) {
+    delete c;
+    return fail(nullptr, RNP_ECUDA, "no CUDA device");
+  }
+  c->st = (cudaStream_t)cuda_stream;
+  c->g = make_geom(*prob);
+  c->coef = make_coef(*prob, c->g);
+  c->B = prob->batch; c->N = prob->N; c->M = prob->M; c->m = prob->m;
+  c->d = c->g.d;
+  c->fp32 = prob->precision == RNP_MIXED;
+  c->plain = prob->exec == RNP_EXEC_PLAIN;
+  c->randnet = prob->corr == RNP_CORR_RANDNET;
+  c->schemeG = prob->gscheme == RNP_G_RK4 ? SCHEME_RK4 : SCHEME_EULER;
+  const double dT = (prob->tN - prob->t0) / prob->N;
+  c->dtF = dT / prob->nF;
+  c->dtG = dT / prob->nG;
+  const int Kmax = std::min(prob->max_iters, prob->N);
+  long long cap = 0;
+  for (int k = 1; k <= Kmax; ++k) cap += prob->N - k + 1;
+  if (prob->max_pairs > 0) cap = prob->max_pairs;
+  c->cap = cap;
+  c->P.assign(c->B, 0);
+  const int B = c->B, N = c->N, M = c->M;
+  const long long d = c->d;
+  char why[256] = {0};
+  rnp_ctx* cc = c;
+  auto bail = [&](rnp_status s, const char* m) {
+    g_create_error = m;
+    destroy_buffers(cc);
+    delete cc;
+    return s;
+  };
+  if (!c->plain) {
+    if (!pick_stencil(c->g, c->fp32, B * N, false, prob->cluster, prob->threads, &c->cfgF, why,
+                      sizeof(why)))
+      return bail(RNP_EINVAL, why);
+    if (!pick_stencil(c->g, c->fp32, B, true, prob->cluster, prob->threads, &c->cfgG, why,
+                      sizeof(why)))
+      return bail(RNP_EINVAL, why);
+  }
+  c->itemcap = B * (N + 1);
+  c->feat_rows_cap = std::max(B * N, B);
+  const int nchF = features_chunks(d), nchN = nn_chunks(d);
+  bool ok = true;
+  ok &= dalloc(&c->U, (size_t)B * (N + 1) * d) == cudaSuccess;
+  ok &= dalloc(&c->Fv, (size_t)B * N * d) == cudaSuccess;
+  ok &= dalloc(&c->Gc, (size_t)B * N * d) == cudaSuccess;
+  ok &= dalloc(&c->Yv, (size_t)B * N * d) == cudaSuccess;
+  ok &= dalloc(&c->gbuf, (size_t)B * d) == cudaSuccess;
+  ok &= dalloc(&c->qbuf, (size_t)B * d) == cudaSuccess;
+  ok &= dalloc(&c->phic, (size_t)B * N * M) == cudaSuccess;
+  ok &= dalloc(&c->phiq, (size_t)B * M) == cudaSuccess;
+  {
+    ok &= dalloc(&c->Sds, (size_t)B * cap * d) == cudaSuccess;
+    ok &= dalloc(&c->Yds, (size_t)B * cap * d) == cudaSuccess;
+    ok &= dalloc(&c->Phi, (size_t)B * cap * M) == cudaSuccess;
+    ok &= dalloc(&c->dist, (size_t)B * cap) == cudaSuccess;
+    ok &= dalloc(&c->nn_part, (size_t)B * cap * nchN) == cudaSuccess;
+  }
+  ok &= dalloc(&c->A, (size_t)M * d) == cudaSuccess;
+  ok &= dalloc(&c->zeta, (size_t)M) == cudaSuccess;
+  ok &= dalloc(&c->sc, (size_t)B * 3) == cudaSuccess;
+  ok &= dalloc(&c->sr, (size_t)B * 3) == cudaSuccess;
+  ok &= dalloc(&c->scale_work, (size_t)B * 3 * 64 * 2) == cudaSuccess;
+  ok &= dalloc(&c->feat_part, (size_t)c->feat_rows_cap * M * nchF) == cudaSuccess;
+  ok &= dalloc(&c->alpha, (size_t)B * RNP_MAX_M) == cudaSuccess;
+  ok &= dalloc(&c->idx, (size_t)B * RNP_MAX_M) == cudaSuccess;
+  ok &= dalloc(&c->meff, (size_t)B) == cudaSuccess;
+  ok &= dalloc(&c->flags, (size_t)4) == cudaSuccess;
+  ok &= dalloc(&c->dP, (size_t)B) == cudaSuccess;
+  ok &= dalloc(&c->err, (size_t)B * (N + 1)) == cudaSuccess;
+  if (c->plain) ok &= dalloc(&c->plain_work, (size_t)4 * B * N * d) == cudaSuccess;
+  ok &= dalloc(&c->d_items, (size_t)4 * c->itemcap) == cudaSuccess;
+  ok &= dalloc(&c->d_app, (size_t)3 * c->itemcap) == cudaSuccess;
+  ok &= dalloc(&c->d_gate, (size_t)(N + 1) * B) == cudaSuccess;
+  ok &= cudaMallocHost((void**)&c->h_items, sizeof(long long) * 4 * c->itemcap) == cudaSuccess;
+  ok &= cudaMallocHost((void**)&c->h_app, sizeof(int) * 3 * c->itemcap) == cudaSuccess;
+  ok &= cudaMallocHost((void**)&c->h_gate, sizeof(int) * (N + 1) * B) == cudaSuccess;
+  ok &= cudaMallocHost((void**)&c->h_err, sizeof(unsigned long long) * B * (N + 1)) == cudaSuccess;
+  ok &= cudaMallocHost((void**)&c->h_flags, sizeof(int) * (4 + RNP_MAX_BATCH)) == cudaSuccess;
+  for (auto& e : c->ev) ok &= cudaEventCreate(&e) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    char m[256];
+    snprintf(m, sizeof(m),
+             "device allocation failed (dataset arena of %lld rows x %lld unknowns per member; "
+             "lower max_iters or max_pairs)",
+             cap, d);
+    return bail(RNP_ENOMEM, m);
+  }
+  if (cudaMemsetAsync(c->dP, 0, sizeof(int) * B, c->st) != cudaSuccess ||
+      cudaMemsetAsync(c->flags, 0, sizeof(int) * 4, c->st) != cudaSuccess ||
+      cudaStreamSynchronize(c->st) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(RNP_ECUDA, "initialisation failed");
+  }
+  for (int i = 0; i < B * 3; ++i) { c->h_c[i] = 0.0; c->h_r[i] = 1.0; }
+  *out = c;
+  return RNP_OK;
+}
+
+rnp_status rnp_destroy(rnp_ctx* c) {
+  if (!c) return RNP_OK;
+  DevGuard gd(c->dev);
+  cudaStreamSynchronize(c->st);
+  destroy_buffers(c);
+  delete c;
+  return RNP_OK;
+}
+
+rnp_status rnp_fine_batch(rnp_ctx* c, const double* U_in, int n, double* U_out) {
+  if (!c) return RNP_EINVAL;
+  c->msg.clear();
+  if (!U_in || !U_out || n < 1 || n > c->N) return fail(c, RNP_EINVAL, "bad arguments");
+  DevGuard gd(c->dev);
+  Items it = affine(c->B * n, 0, c->d, 0, c->d, nullptr);
+  if (!c->plain && c->B * n > c->B * c->N) return fail(c, RNP_EINVAL, "too many items");
+  return run_stencil(c, true, U_in, U_out, nullptr, it);
+}
+
+rnp_status rnp_get_weights(rnp_ctx* c, double* A, double* zeta) {
+  if (!c) return RNP_EINVAL;
+  c->msg.clear();
+  DevGuard gd(c->dev);
+  rnp_status s = ensure_weights(c);
+  if (s) return s;
+  if (A) CK(cudaMemcpyAsync(A, c->A, sizeof(double) * c->M * c->d, cudaMemcpyDeviceToDevice, c->st));
+  if (zeta) CK(cudaMemcpyAsync(zeta, c->zeta, sizeof(double) * c->M, cudaMemcpyDeviceToDevice, c->st));
+  return RNP_OK;
+}
+
+rnp_status rnp_set_scaling(rnp_ctx* c, const double* hc, const double* hr) {
+  if (!c) return RNP_EINVAL;
+  c->msg.clear();
+  if (!hc || !hr) return fail(c, RNP_EINVAL, "NULL scaling");
+  DevGuard gd(c->dev);
+  for (int i = 0; i < c->B * 3; ++i) {
+    if (!(hr[i] != 0.0)) return fail(c, RNP_EINVAL, "scale r must be nonzero");
+    c->h_c[i] = hc[i];
+    c->h_r[i] = hr[i];
+  }
+  CK(cudaMemcpyAsync(c->sc, c->h_c, sizeof(double) * c->B * 3, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->sr, c->h_r, sizeof(double) * c->B * 3, cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  c->scaling_ready = true;
+  return RNP_OK;
+}
+
+rnp_status rnp_get_scaling(rnp_ctx* c, double* hc, double* hr) {
+  if (!c) return RNP_EINVAL;
+  c->msg.clear();
+  DevGuard gd(c->dev);
+  if (!c->scaling_ready) {
+    for (int i = 0; i < c->B * 3; ++i) { hc[i] = 0.0; hr[i] = 1.0; }
+    return RNP_OK;
+  }
+  CK(cudaMemcpyAsync(hc, c->sc, sizeof(double) * c->B * 3, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(hr, c->sr, sizeof(double) * c->B * 3, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return RNP_OK;
+}
+
+rnp_status rnp_reset(rnp_ctx* c) {
+  if (!c) return RNP_EINVAL;
+  c->msg.clear();
+  DevGuard gd(c->dev);
+  std::fill(c->P.begin(), c->P.end(), 0);
+  c->scaling_ready = false;
+  return upload_P(c);
+}
+
+rnp_status rnp_get_pairs(rnp_ctx* c, long long* pairs) {
+  if (!c || !pairs) return RNP_EINVAL;
+  for (int b = 0; b < c->B; ++b) pairs[b] = c->P[b];
+  return RNP_OK;
+}
+
+static rnp_status ensure_scaling_identity(rnp_ctx* c) {
+  if (c->scaling_ready) return RNP_OK;
+  double hc[RNP_MAX_BATCH * 3], hr[RNP_MAX_BATCH * 3];
+  for (int i = 0; i < c->B * 3; ++i) { hc[i] = 0.0; hr[i] = 1.0; }
+  return rnp_set_scaling(c, hc, hr);
+}
+
+rnp_status rnp_randnet_fit(rnp_ctx* c, const double* Uin, const double* Y, int P) {
+  if (!c) return RNP_EINVAL;
+  c->msg.clear();
+  if (!Uin || !Y || P < 0) return fail(c, RNP_EINVAL, "bad arguments");
+  if (P == 0) return RNP_OK;
+  DevGuard gd(c->dev);
+  for (int b = 0; b < c->B; ++b)
+    if (c->P[b] + (long long)P > c->cap)
+      return fail(c, RNP_ENOMEM, "dataset arena full (%lld rows per member)", c->cap);
+  rnp_status s = ensure_weights(c);
+  if (s) return s;
+  if ((s = ensure_scaling_identity(c))) return s;
+  // rows in chunks that fit the offset tables and the feature workspace
+  const int chunk = std::min(c->itemcap, c->feat_rows_cap);
+  const int R = c->B * P;
+  long long* src = c->h_items;
+  long long* sdst = c->h_items + c->itemcap;
+  long long* pdst = c->h_items + 2 * c->itemcap;
+  int* rowb = c->h_app;
+  for (int r0 = 0; r0 < R; r0 += chunk) {
+    const int n = std::min(chunk, R - r0);
+    for (int r = 0; r < n; ++r) {
+      const int b = (r0 + r) / P, t = (r0 + r) % P;
+      src[r] = ((long long)b * P + t) * c->d;
+      sdst[r] = ((long long)b * c->cap + c->P[b] + t) * c->d;
+      pdst[r] = ((long long)b * c->cap + c->P[b] + t) * c->M;
+      rowb[r] = b;
+    }
+    CK(cudaMemcpyAsync(c->d_items, c->h_items, sizeof(long long) * 3 * c->itemcap,
+                       cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->d_app, c->h_app, sizeof(int) * c->itemcap, cudaMemcpyHostToDevice,
+                       c->st));
+    Rows rsrc{c->d_items, 0, 0}, rdst{c->d_items + c->itemcap, 0, 0};
+    CK(launch_scale_rows(c->g, Uin, rsrc, c->d_app, 1, c->sc, c->sr, c->Sds, rdst, n, nullptr,
+                         c->st));
+    CK(launch_copy_rows(Y, c->d_items, c->Yds, c->d_items + c->itemcap, c->d, n, c->st));
+    Rows prow{c->d_items + 2 * c->itemcap, 0, 0};
+    CK(launch_features64(c->A, c->zeta, c->M, c->d, c->Sds, rdst, n, c->Phi, prow,
+                         c->feat_part, nullptr, c->st));
+    CK(cudaStreamSynchronize(c->st));  // the staging tables are reused
+  }
+  for (int b = 0; b < c->B; ++b) c->P[b] += P;
+  return upload_P(c);
+}
+
+rnp_status rnp_randnet_predict(rnp_ctx* c, const double* q, double* out) {
+  if (!c) return RNP_EINVAL;
+  c->msg.clear();
+  if (!q || !out) return fail(c, RNP_EINVAL, "bad arguments");
+  DevGuard gd(c->dev);
+  rnp_status s = ensure_weights(c);
+  if (s) return s;
+  if ((s = ensure_scaling_identity(c))) return s;
+  CK(cudaMemsetAsync(c->flags, 0, sizeof(int) * 4, c->st));
+  if ((s = predict_core(c, q, 0, c->d, c->phiq, 0, c->M, nullptr))) return s;
+  CK(launch_update(nullptr, 0, c->Yds, c->cap, c->d, c->alpha, c->idx, c->meff, out, c->d,
+                   nullptr, 0, c->flags + 2, c->B, nullptr, c->st));
+  int esc, fl, nf;
+  if ((s = read_flags(c, &esc, &fl, &nf))) return s;
+  if (fl) return fail(c, RNP_ENONFINITE, "ridge system not positive definite");
+  return RNP_OK;
+}
+
+rnp_status rnp_coarse_sweep(rnp_ctx* c, int first, const double* U_first, double* U) {
+  if (!c) return RNP_EINVAL;
+  c->msg.clear();
+  if (!U_first || !U || first < 0 || first > c->N) return fail(c, RNP_EINVAL, "bad arguments");
+  DevGuard gd(c->dev);
+  const long long d = c->d, sb = (long long)(c->N + 1) * d;
+  CK(cudaMemcpy2DAsync(U + (long long)first * d, sizeof(double) * sb, U_first,
+                       sizeof(double) * d, sizeof(double) * d, c->B, cudaMemcpyDeviceToDevice,
+                       c->st));
+  const bool use_fhat = c->randnet && Pmax(c) > 0;
+  rnp_status s;
+  if (use_fhat) {
+    if ((s = ensure_weights(c))) return s;
+    if ((s = ensure_scaling_identity(c))) return s;
+  }
+  CK(cudaMemsetAsync(c->flags, 0, sizeof(int) * 4, c->st));
+  for (int i = first + 1; i <= c->N; ++i) {
+    if (!use_fhat) {
+      Items it = affine(c->B, (long long)(i - 1) * d, sb, (long long)i * d, sb, nullptr);
+      if ((s = run_stencil(c, false, U, U, nullptr, it))) return s;
+      continue;
+    }
+    Items it = affine(c->B, (long long)(i - 1) * d, sb, 0, d, nullptr);
+    if ((s = run_stencil(c, false, U, c->gbuf, nullptr, it))) return s;
+    if ((s = predict_core(c, U, (long long)(i - 1) * d, sb, c->phiq, 0, c->M, nullptr))) return s;
+    CK(launch_update(c->gbuf, d, c->Yds, c->cap, d, c->alpha, c->idx, c->meff,
+                     U + (long long)i * d, sb, nullptr, 0, c->flags + 2, c->B, nullptr, c->st));
+  }
+  if (first == 0 && !use_fhat && c->p.scale_mode == RNP_SCALE_MINMAX) {
+    CK(launch_scaling(c->g, U, sb, c->N + 1, c->B, false, c->sc, c->sr, c->scale_work,
+                      c->flags + 2, c->st));
+    c->scaling_ready = true;
+  }
+  int esc, fl, nf;
+  if ((s = read_flags(c, &esc, &fl, &nf))) return s;
+  if (fl) return fail(c, RNP_ENONFINITE, "ridge system not positive definite");
+  if (nf) return fail(c, RNP_ENONFINITE, "non-finite state in the sweep");
+  return RNP_OK;
+}
+
+rnp_status rnp_solve(rnp_ctx* c, const double* u0, double* Uout, rnp_stats* stats) {
+  if (!c) return RNP_EINVAL;
+  c->msg.clear();
+  if (!u0 || !Uout) return fail(c, RNP_EINVAL, "bad arguments");
+  DevGuard gd(c->dev);
+  auto t_start = std::chrono::steady_clock::now();
+  const long long launches0 = launches_total();
+  const int B = c->B, N = c->N, M = c->M;
+  const long long d = c->d, sb = (long long)(N + 1) * d, nb = (long long)N * d;
+  rnp_stats st;
+  memset(&st, 0, sizeof(st));
+  rnp_status s;
+  float ms;
+
+  std::fill(c->P.begin(), c->P.end(), 0);
+  if ((s = upload_P(c))) return s;
+  CK(cudaMemsetAsync(c->flags, 0, sizeof(int) * 4, c->st));
+
+  // k = 0: U_i^0 = G(U_{i-1}^0), G values kept for the first targets.
+  CK(cudaMemcpy2DAsync(c->U, sizeof(double) * sb, u0, sizeof(double) * d, sizeof(double) * d, B,
+                       cudaMemcpyDeviceToDevice, c->st));
+  CK(cudaEventRecord(c->ev[0], c->st));
+  for (int i = 1; i <= N; ++i) {
+    Items it = affine(B, (long long)(i - 1) * d, sb, (long long)i * d, sb, nullptr);
+    it.dst2_base = (long long)(i - 1) * d;
+    it.dst2_stride = nb;
+    if ((s = run_stencil(c, false, c->U, c->U, c->Gc, it))) return s;
+  }
+  CK(launch_scaling(c->g, c->U, sb, N + 1, B, c->p.scale_mode == RNP_SCALE_NONE, c->sc, c->sr,
+                    c->scale_work, c->flags + 2, c->st));
+  c->scaling_ready = true;
+  if (c->randnet && (s = ensure_weights(c))) return s;
+  CK(cudaEventRecord(c->ev[1], c->st));
+  CK(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaEventSynchronize(c->ev[1]));
+  CK(cudaStreamSynchronize(c->st));
+  if (c->h_flags[2]) return fail(c, RNP_ENONFINITE, "non-finite state in the k = 0 sweep");
+  CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+  st.t_sweep_ms += ms;
+
+  std::vector<int> L(B, 0), done(B, 0), K(B, 0);
+  const int Kmax = std::min(c->p.max_iters, N);
+  int status = RNP_OK;
+  for (int k = 1; k <= Kmax; ++k) {
+    // ---- parallel fine step over the unconverged starts ----------------
+    int nit = 0;
+    long long* srco = c->h_items;
+    long long* dsto = c->h_items + c->itemcap;
+    long long* soff = c->h_items + 2 * c->itemcap;
+    long long* poff = c->h_items + 3 * c->itemcap;
+    int* ab = c->h_app;
+    int* aj = c->h_app + c->itemcap;
+    int* ap = c->h_app + 2 * c->itemcap;
+    for (int b = 0; b < B; ++b) {
+      if (done[b]) continue;
+      if (c->randnet && c->P[b] + (N - L[b]) > c->cap)
+        return fail(c, RNP_ENOMEM, "dataset arena full (%lld rows per member)", c->cap);
+      for (int j = L[b]; j < N; ++j) {
+        const int p = c->P[b] + (j - L[b]);
+        srco[nit] = (long long)b * sb + (long long)j * d;
+        dsto[nit] = (long long)b * nb + (long long)j * d;
+        soff[nit] = ((long long)b * c->cap + p) * d;
+        poff[nit] = ((long long)b * c->cap + p) * M;
+        ab[nit] = b; aj[nit] = j; ap[nit] = p;
+        ++nit;
+      }
+    }
+    for (int i = 0; i <= N; ++i)
+      for (int b = 0; b < B; ++b) c->h_gate[i * B + b] = (!done[b] && i >= L[b] + 2) ? 1 : 0;
+    CK(cudaMemcpyAsync(c->d_items, c->h_items, sizeof(long long) * 4 * c->itemcap,
+                       cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->d_app, c->h_app, sizeof(int) * 3 * c->itemcap, cudaMemcpyHostToDevice,
+                       c->st));
+    CK(cudaMemcpyAsync(c->d_gate, c->h_gate, sizeof(int) * (N + 1) * B, cudaMemcpyHostToDevice,
+                       c->st));
+    CK(cudaMemsetAsync(c->err, 0, sizeof(unsigned long long) * B * (N + 1), c->st));
+    CK(cudaEventRecord(c->ev[0], c->st));
+    Items fit{};
+    fit.src_off = c->d_items;
+    fit.dst_off = c->d_items + c->itemcap;
+    fit.n = nit;
+    if ((s = run_stencil(c, true, c->U, c->Fv, nullptr, fit))) return s;
+    CK(cudaEventRecord(c->ev[1], c->st));
+    for (int b = 0; b < B; ++b)
+      if (!done[b]) st.fine_cell_updates += (long long)(N - L[b]) * c->p.nF * d;
+
+    // ---- dataset append (Eq. 6) and features of the new rows -----------
+    AppendItems ai{c->d_app, c->d_app + c->itemcap, c->d_app + 2 * c->itemcap, nit};
+    CK(launch_append(c->g, c->U, sb, c->Fv, c->Gc, nb, c->Yv, c->Sds, c->Yds, c->cap, c->sc,
+                     c->sr, ai, c->randnet, c->st));
+    if (c->randnet) {
+      if (k == 1) {
+        Rows srows{c->d_items + 2 * c->itemcap, 0, 0};
+        Rows prow{c->d_items + 3 * c->itemcap, 0, 0};
+        CK(launch_features64(c->A, c->zeta, M, d, c->Sds, srows, nit, c->Phi, prow,
+                             c->feat_part, nullptr, c->st));
+      } else {
+        CK(launch_copy_phi(c->phic, (long long)N * M, c->Phi, c->cap, M, ai, c->st));
+      }
+      for (int b = 0; b < B; ++b)
+        if (!done[b]) c->P[b] += N - L[b];
+      for (int b = 0; b < B; ++b) c->h_flags[4 + b] = c->P[b];
+      CK(cudaMemcpyAsync(c->dP, c->h_flags + 4, sizeof(int) * B, cudaMemcpyHostToDevice, c->st));
+    }
+    // ---- exact leftmost slice: U_{L+1} = F(U_L) ------------------------
+    for (int b = 0; b < B; ++b)
+      if (!done[b])
+        CK(cudaMemcpyAsync(c->U + (long long)b * sb + (long long)(L[b] + 1) * d,
+                           c->Fv + (long long)b * nb + (long long)L[b] * d, sizeof(double) * d,
+                           cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaEventRecord(c->ev[2], c->st));
+
+    // ---- sequential predictor-corrector sweep (Eq. 3) ------------------
+    int imin = N + 1;
+    for (int b = 0; b < B; ++b)
+      if (!done[b]) imin = std::min(imin, L[b] + 2);
+    for (int i = imin; i <= N; ++i) {
+      const int* gate = c->d_gate + (long long)i * B;
+      Items it = affine(B, (long long)(i - 1) * d, sb, 0, d, gate);
+      it.dst2_base = (long long)(i - 1) * d;
+      it.dst2_stride = nb;
+      if ((s = run_stencil(c, false, c->U, c->gbuf, c->Gc, it))) return s;
+      if (c->randnet) {
+        if ((s = predict_core(c, c->U, (long long)(i - 1) * d, sb, c->phic,
+                              (long long)(i - 1) * M, (long long)N * M, gate)))
+          return s;
+        CK(launch_update(c->gbuf, d, c->Yds, c->cap, d, c->alpha, c->idx, c->meff,
+                         c->U + (long long)i * d, sb, c->err + i, N + 1, c->flags + 2, B, gate,
+                         c->st));
+      } else {
+        CK(launch_update_para(c->gbuf, d, c->Yv + (long long)(i - 1) * d, nb, d,
+                              c->U + (long long)i * d, sb, c->err + i, N + 1, c->flags + 2, B,
+                              gate, c->st));
+      }
+    }
+    CK(cudaEventRecord(c->ev[3], c->st));
+    CK(cudaMemcpyAsync(c->h_err, c->err, sizeof(unsigned long long) * B * (N + 1),
+                       cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+    st.t_fine_ms += ms;
+    CK(cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]));
+    st.t_fit_ms += ms;
+    CK(cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]));
+    st.t_sweep_ms += ms;
+    if (c->h_flags[1]) return fail(c, RNP_ENONFINITE, "ridge system not positive definite");
+    if (c->h_flags[2]) return fail(c, RNP_ENONFINITE, "non-finite state at iteration %d", k);
+
+    // ---- stopping rule (Eq. 5) -----------------------------------------
+    bool all = true;
+    for (int b = 0; b < B; ++b) {
+      if (done[b]) continue;
+      int Ln = L[b] + 1;
+      for (int i = L[b] + 2; i <= N; ++i) {
+        double e;
+        memcpy(&e, &c->h_err[(long long)b * (N + 1) + i], sizeof(double));
+        if (e < c->p.tol) Ln = i; else break;
+      }
+      L[b] = Ln;
+      K[b] = k;
+      if (L[b] == N) done[b] = 1;
+      all &= done[b] != 0;
+    }
+    if (all) break;
+  }
+  st.lambda_escalations = c->h_flags[0];
+  CK(cudaMemcpyAsync(Uout, c->U, sizeof(double) * B * sb, cudaMemcpyDeviceToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  st.converged = 1;
+  st.L = N;
+  for (int b = 0; b < B; ++b) {
+    st.K = std::max(st.K, K[b]);
+    st.K_each[b] = K[b];
+    st.L = std::min(st.L, L[b]);
+    st.converged &= done[b];
+    st.pairs += c->P[b];
+  }
+  if (!st.converged) status = RNP_ENOTCONV;
+  st.t_total_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  st.kernel_launches = launches_total() - launches0;
+  if (stats) *stats = st;
+  if (status == RNP_ENOTCONV) return fail(c, RNP_ENOTCONV, "not converged after %d iterations", Kmax);
+  return RNP_OK;
+}
+
+}  // extern "C"

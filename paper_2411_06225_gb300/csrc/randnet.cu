@@ -1,0 +1,649 @@
+// randnet.cu -- the RandNet correction of Eq. randnet: seeded random weights
+// (Alg. 3), per-species rescaling (Alg. 1 initialisation), random features
+// phi = ReLU(A s + zeta) (Eq. HA), the m-nearest-neighbour restriction of
+// App. B, the ridge readout of Eq. ridgeless in its dual m x m form, and
+// the predictor-corrector update of Eq. 3 fused with the max-norm of Eq. 5.
+//
+// Reductions over the state dimension d are split into fixed chunks whose
+// partial sums are combined in a fixed order, so every result is
+// reproducible run to run.  The m x m ridge system is assembled and solved
+// with explicitly rounded FP64 operations in the order of the plain serial
+// formulas.
+#include <atomic>
+#include <cstdint>
+
+#include "rnp_internal.h"
+
+namespace rnp {
+
+static std::atomic<long long> g_launches{0};
+long long launches_total() { return g_launches.load(); }
+void count_launches(long long n) { g_launches += n; }
+
+static int grid_cap(long long tot, int threads, int cap = 152 * 16) {
+  long long b = (tot + threads - 1) / threads;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+// ---------------------------------------------------------------------------
+// Weights: SplitMix64 (Steele, Lea & Flood 2014) in counter form.  Draw
+// number (stream * 2^40 + idx + 1) of the generator seeded with `seed` is
+// mix(seed + n * gamma); u = top 53 bits * 2^-53;  value = 2u - 1.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double sm64_uniform(uint64_t seed, uint32_t stream,
+                                               uint64_t idx) {
+  const uint64_t n = ((uint64_t)stream << 40) + idx + 1;
+  const uint64_t z = sm64_mix(seed + n * 0x9e3779b97f4a7c15ULL);
+  return __dmul_rn((double)(z >> 11), 1.0 / 9007199254740992.0);
+}
+
+// Round-to-nearest-even of a double to bfloat16 (8 significant bits), done
+// on the double's bits so that there is a single rounding.
+__device__ __forceinline__ uint16_t to_bf16_rne(double x) {
+  uint64_t b = (uint64_t)__double_as_longlong(x);
+  const uint64_t lsb = (b >> 45) & 1ULL;
+  b += 0x00000FFFFFFFFFFFULL + lsb;
+  b &= ~((1ULL << 45) - 1ULL);
+  const float f = (float)__longlong_as_double((long long)b);  // exact
+  return (uint16_t)(__float_as_uint(f) >> 16);
+}
+
+__global__ void k_weights(uint64_t seed, int M, long long d, double* A, double* zeta,
+                          float* A32, uint16_t* Abf, float* zeta32) {
+  const long long tot = (long long)M * d;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    const double v = __dsub_rn(__dmul_rn(2.0, sm64_uniform(seed, 0, (uint64_t)t)), 1.0);
+    if (A) A[t] = v;
+    if (A32) A32[t] = (float)v;
+    if (Abf) Abf[t] = to_bf16_rne(v);
+    if (t < M) {
+      const double z = __dsub_rn(__dmul_rn(2.0, sm64_uniform(seed, 1, (uint64_t)t)), 1.0);
+      if (zeta) zeta[t] = z;
+      if (zeta32) zeta32[t] = (float)z;
+    }
+  }
+}
+
+cudaError_t launch_weights(uint64_t seed, int M, long long d, double* A, double* zeta,
+                           float* A32, uint16_t* Abf16, float* zeta32, cudaStream_t st) {
+  const long long tot = (long long)M * d;
+  count_launches(1);
+  k_weights<<<grid_cap(tot, 256), 256, 0, st>>>(seed, M, d, A, zeta, A32, Abf16, zeta32);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Per-species scaling
+// ---------------------------------------------------------------------------
+__global__ void k_minmax_partial(const double* U, long long bstride, int nstates,
+                                 long long n, long long d, int ncomp, double* work,
+                                 int nchunk, int* nonfinite) {
+  // blockIdx.y = b * ncomp + q ; blockIdx.x = chunk
+  const int bq = blockIdx.y;
+  const int b = bq / ncomp, q = bq - b * ncomp;
+  const long long tot = (long long)nstates * n;
+  double mn = 1.0 / 0.0, mx = -1.0 / 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)nchunk * blockDim.x) {
+    const long long s = t / n, j = t - s * n;
+    const double v = U[b * bstride + s * d + q * n + j];
+    if (nonfinite && !isfinite(v)) *nonfinite = 1;
+    mn = v < mn ? v : mn;
+    mx = v > mx ? v : mx;
+  }
+  __shared__ double smn[256], smx[256];
+  smn[threadIdx.x] = mn;
+  smx[threadIdx.x] = mx;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      const double a = smn[threadIdx.x + o], c = smx[threadIdx.x + o];
+      if (a < smn[threadIdx.x]) smn[threadIdx.x] = a;
+      if (c > smx[threadIdx.x]) smx[threadIdx.x] = c;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    work[(bq * (long long)nchunk + blockIdx.x) * 2] = smn[0];
+    work[(bq * (long long)nchunk + blockIdx.x) * 2 + 1] = smx[0];
+  }
+}
+
+__global__ void k_minmax_finish(const double* work, int nchunk, int B, int ncomp,
+                                bool none, double* c, double* r) {
+  const int bq = blockIdx.x * blockDim.x + threadIdx.x;
+  if (bq >= B * ncomp) return;
+  const int b = bq / ncomp, q = bq - b * ncomp;
+  if (none) {
+    c[b * 3 + q] = 0.0;
+    r[b * 3 + q] = 1.0;
+    return;
+  }
+  double mn = work[(bq * (long long)nchunk) * 2], mx = work[(bq * (long long)nchunk) * 2 + 1];
+  for (int k = 1; k < nchunk; ++k) {
+    const double a = work[(bq * (long long)nchunk + k) * 2];
+    const double e = work[(bq * (long long)nchunk + k) * 2 + 1];
+    if (a < mn) mn = a;
+    if (e > mx) mx = e;
+  }
+  const double cc = __dmul_rn(0.5, __dadd_rn(mx, mn));
+  double rr = __dmul_rn(0.5, __dsub_rn(mx, mn));
+  if (rr == 0.0) rr = 1.0;
+  c[b * 3 + q] = cc;
+  r[b * 3 + q] = rr;
+}
+
+static const int kScaleChunks = 64;
+
+cudaError_t launch_scaling(const Geom& g, const double* U, long long bstride, int nstates,
+                           int B, bool none, double* c, double* r, double* work,
+                           int* nonfinite, cudaStream_t st) {
+  dim3 grid(kScaleChunks, B * g.ncomp);
+  count_launches(1);
+  k_minmax_partial<<<grid, 256, 0, st>>>(U, bstride, nstates, g.n, g.d, g.ncomp, work,
+                                         kScaleChunks, nonfinite);
+  count_launches(1);
+  k_minmax_finish<<<(B * g.ncomp + 63) / 64, 64, 0, st>>>(work, kScaleChunks, B, g.ncomp,
+                                                          none, c, r);
+  return cudaGetLastError();
+}
+
+__global__ void k_scale_rows(const double* U, Rows src, const int* row_b, int row_b_div,
+                             const double* c, const double* r, double* S, Rows dst, int R,
+                             long long n, long long d, const int* gate) {
+  const long long tot = (long long)R * d;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int row = (int)(t / d);
+    if (gate && !gate[row]) continue;
+    const long long e = t - (long long)row * d;
+    const int q = (int)(e / n);
+    const int b = row_b ? row_b[row] : row / row_b_div;
+    const double u = U[item_off(src.off, src.base, src.stride, row) + e];
+    S[item_off(dst.off, dst.base, dst.stride, row) + e] =
+        __ddiv_rn(__dsub_rn(u, c[b * 3 + q]), r[b * 3 + q]);
+  }
+}
+
+cudaError_t launch_scale_rows(const Geom& g, const double* U, Rows src, const int* row_b,
+                              int row_b_div, const double* c, const double* r, double* S,
+                              Rows dst, int R, const int* gate, cudaStream_t st) {
+  if (R <= 0) return cudaSuccess;
+  count_launches(1);
+  k_scale_rows<<<grid_cap((long long)R * g.d, 256), 256, 0, st>>>(
+      U, src, row_b, row_b_div, c, r, S, dst, R, g.n, g.d, gate);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Random features, FP64 (Eq. HA).  Stage 1: for a chunk of CH coordinates
+// and a group of TR rows, every warp owns a set of neurons w and computes the
+// TR partial dot products A[w, chunk] . s[r, chunk] (lanes stride the chunk,
+// then a fixed butterfly reduction).  Stage 2 sums the chunk partials in
+// chunk order, adds zeta and applies ReLU.
+// ---------------------------------------------------------------------------
+static const int kFeatCH = 1024;
+static const int kFeatTR = 4;
+
+int features_chunks(long long d) { return (int)((d + kFeatCH - 1) / kFeatCH); }
+
+__global__ void __launch_bounds__(256) k_feat_partial(const double* A, int M, long long d,
+                                                      const double* S, Rows rows, int R,
+                                                      double* part, int nch,
+                                                      const int* gate) {
+  __shared__ double sS[kFeatTR][kFeatCH];
+  const int ch = blockIdx.x;
+  const int r0 = blockIdx.y * kFeatTR;
+  const long long j0 = (long long)ch * kFeatCH;
+  const int len = (int)((d - j0) < kFeatCH ? (d - j0) : kFeatCH);
+  bool any = false;
+  for (int r = 0; r < kFeatTR; ++r) {
+    const int row = r0 + r;
+    const bool on = row < R && (!gate || gate[row]);
+    any |= on;
+    const double* src = on ? S + item_off(rows.off, rows.base, rows.stride, row) + j0 : nullptr;
+    for (int j = threadIdx.x; j < kFeatCH; j += blockDim.x)
+      sS[r][j] = (on && j < len) ? src[j] : 0.0;
+  }
+  if (!any) return;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nw = blockDim.x >> 5;
+  for (int w = warp; w < M; w += nw) {
+    const double* Aw = A + (long long)w * d + j0;
+    double acc[kFeatTR];
+#pragma unroll
+    for (int r = 0; r < kFeatTR; ++r) acc[r] = 0.0;
+    for (int j = lane; j < len; j += 32) {
+      const double a = Aw[j];
+#pragma unroll
+      for (int r = 0; r < kFeatTR; ++r) acc[r] = fma(a, sS[r][j], acc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < kFeatTR; ++r) {
+      double v = acc[r];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      acc[r] = v;
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int r = 0; r < kFeatTR; ++r)
+        if (r0 + r < R) part[((long long)(r0 + r) * M + w) * nch + ch] = acc[r];
+    }
+  }
+}
+
+__global__ void k_feat_finish(const double* part, int nch, int R, int M, const double* zeta,
+                              double* phi, Rows prow, const int* gate) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= R * M) return;
+  const int row = t / M, w = t - row * M;
+  if (gate && !gate[row]) return;
+  const double* p = part + (long long)t * nch;
+  double acc = 0.0;
+  for (int k = 0; k < nch; ++k) acc = acc + p[k];
+  const double v = acc + zeta[w];
+  phi[item_off(prow.off, prow.base, prow.stride, row) + w] = v > 0.0 ? v : 0.0;
+}
+
+cudaError_t launch_features64(const double* A, const double* zeta, int M, long long d,
+                              const double* S, Rows s_rows, int R, double* phi,
+                              Rows phi_rows, double* part, const int* gate,
+                              cudaStream_t st) {
+  if (R <= 0) return cudaSuccess;
+  const int nch = features_chunks(d);
+  dim3 grid(nch, (R + kFeatTR - 1) / kFeatTR);
+  count_launches(1);
+  k_feat_partial<<<grid, 256, 0, st>>>(A, M, d, S, s_rows, R, part, nch, gate);
+  count_launches(1);
+  k_feat_finish<<<(R * M + 255) / 256, 256, 0, st>>>(part, nch, R, M, zeta, phi, phi_rows,
+                                                     gate);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Nearest-neighbour distances (App. B): delta_p = sum_j (q_j - S_pj)^2.
+// One warp per stored row and chunk; chunk partials are summed in order by
+// the selection kernel.
+// ---------------------------------------------------------------------------
+static const int kNnCH = 4096;
+static const int kNnRows = 8;
+
+int nn_chunks(long long d) { return (int)((d + kNnCH - 1) / kNnCH); }
+
+__global__ void __launch_bounds__(256) k_nn_partial(const double* q, const double* S,
+                                                    long long cap, long long d, const int* P,
+                                                    double* part, int nch, const int* gate) {
+  const int b = blockIdx.z;
+  if (gate && !gate[b]) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p = blockIdx.y * kNnRows + warp;
+  if (p >= P[b]) return;
+  const int ch = blockIdx.x;
+  const long long j0 = (long long)ch * kNnCH;
+  const long long j1 = (j0 + kNnCH) < d ? j0 + kNnCH : d;
+  const double* qb = q + (long long)b * d;
+  const double* Sp = S + ((long long)b * cap + p) * d;
+  double acc = 0.0;
+  for (long long j = j0 + lane; j < j1; j += 32) {
+    const double t = qb[j] - Sp[j];
+    acc = fma(t, t, acc);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) part[((long long)b * cap + p) * nch + ch] = acc;
+}
+
+cudaError_t launch_nn_partial(const double* q, const double* S, long long cap, long long d,
+                              const int* P, int Pmax, int B, double* part, const int* gate,
+                              cudaStream_t st) {
+  if (Pmax <= 0 || B <= 0) return cudaSuccess;
+  const int nch = nn_chunks(d);
+  dim3 grid(nch, (Pmax + kNnRows - 1) / kNnRows, B);
+  count_launches(1);
+  k_nn_partial<<<grid, 256, 0, st>>>(q, S, cap, d, P, part, nch, gate);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Top-m selection + dual ridge solve, one CTA per member.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool lex_less(double a, int ia, double b, int ib) {
+  return a < b || (a == b && ia < ib);
+}
+
+__global__ void __launch_bounds__(256) k_topm_ridge(const double* part, int nch,
+                                                    const double* Phi, long long cap, int M,
+                                                    const double* phiq, long long phiq_bstride,
+                                                    const int* Pn, int m, double lambda,
+                                                    double* dist, double* alpha, int* idx,
+                                                    int* meff, int* esc_count, int* fail,
+                                                    const int* gate) {
+  const int b = blockIdx.x;
+  if (gate && !gate[b]) return;
+  const int P = Pn[b];
+  const int me = m < P ? m : P;
+  __shared__ int sel[RNP_MAX_M];
+  __shared__ double wd[32];
+  __shared__ int wi[32];
+  __shared__ double Kraw[RNP_MAX_M * RNP_MAX_M];
+  __shared__ double L[RNP_MAX_M * RNP_MAX_M];
+  __shared__ double rhs[RNP_MAX_M], y[RNP_MAX_M], x[RNP_MAX_M];
+  double* db = dist + (long long)b * cap;
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    const double* pp = part + ((long long)b * cap + p) * nch;
+    double acc = 0.0;
+    for (int k = 0; k < nch; ++k) acc = acc + pp[k];
+    db[p] = acc;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int l = 0; l < me; ++l) {
+    double bd = 1.0 / 0.0;
+    int bi = 0x7fffffff;
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+      bool taken = false;
+      for (int k = 0; k < l; ++k) taken |= (sel[k] == p);
+      if (taken) continue;
+      double v = db[p];
+      if (v != v) v = 1.0 / 0.0;  // a NaN distance ranks last, never unselected
+      if (lex_less(v, p, bd, bi)) { bd = v; bi = p; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double od = __shfl_xor_sync(0xffffffffu, bd, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (lex_less(od, oi, bd, bi)) { bd = od; bi = oi; }
+    }
+    if (lane == 0) { wd[warp] = bd; wi[warp] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double xd = wd[0];
+      int xi = wi[0];
+      for (int k = 1; k < nw; ++k)
+        if (lex_less(wd[k], wi[k], xd, xi)) { xd = wd[k]; xi = wi[k]; }
+      sel[l] = xi;
+    }
+    __syncthreads();
+  }
+  // Gram entries K[i][j] = sum_w X_i,w X_j,w (i >= j) and rhs_i = X_i . phi_q,
+  // summed over w in ascending order.
+  const double* X = Phi + (long long)b * cap * M;
+  const double* pq = phiq + (long long)b * phiq_bstride;
+  const int nK = me * (me + 1) / 2;
+  for (int t = threadIdx.x; t < nK + me; t += blockDim.x) {
+    if (t < nK) {
+      int i = 0;
+      while ((i + 1) * (i + 2) / 2 <= t) ++i;
+      const int j = t - i * (i + 1) / 2;
+      const double* xi = X + (long long)sel[i] * M;
+      const double* xj = X + (long long)sel[j] * M;
+      double acc = 0.0;
+      for (int w = 0; w < M; ++w) acc = __dadd_rn(acc, __dmul_rn(xi[w], xj[w]));
+      Kraw[i * RNP_MAX_M + j] = acc;
+    } else {
+      const int i = t - nK;
+      const double* xi = X + (long long)sel[i] * M;
+      double acc = 0.0;
+      for (int w = 0; w < M; ++w) acc = __dadd_rn(acc, __dmul_rn(xi[w], pq[w]));
+      rhs[i] = acc;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  meff[b] = me;
+  for (int l = 0; l < me; ++l) idx[b * RNP_MAX_M + l] = sel[l];
+  if (me == 0) return;
+  double lam = lambda;
+  int ok = 0, tries = 0;
+  for (tries = 0; tries <= 4 && !ok; ++tries) {
+    ok = 1;
+    for (int j = 0; j < me && ok; ++j) {
+      double s = __dadd_rn(Kraw[j * RNP_MAX_M + j], lam);
+      for (int k = 0; k < j; ++k) s = __dsub_rn(s, __dmul_rn(L[j * RNP_MAX_M + k], L[j * RNP_MAX_M + k]));
+      if (!(s > 0.0)) { ok = 0; break; }
+      const double ljj = __dsqrt_rn(s);
+      L[j * RNP_MAX_M + j] = ljj;
+      for (int i = j + 1; i < me; ++i) {
+        double t = Kraw[i * RNP_MAX_M + j];
+        for (int k = 0; k < j; ++k) t = __dsub_rn(t, __dmul_rn(L[i * RNP_MAX_M + k], L[j * RNP_MAX_M + k]));
+        L[i * RNP_MAX_M + j] = __ddiv_rn(t, ljj);
+      }
+    }
+    if (!ok) lam = __dmul_rn(lam, 10.0);
+  }
+  if (!ok) {
+    atomicExch(fail, 1);
+    for (int l = 0; l < me; ++l) alpha[b * RNP_MAX_M + l] = 0.0;
+    return;
+  }
+  if (tries - 1 > 0) atomicAdd(esc_count, tries - 1);
+  for (int i = 0; i < me; ++i) {
+    double t = rhs[i];
+    for (int k = 0; k < i; ++k) t = __dsub_rn(t, __dmul_rn(L[i * RNP_MAX_M + k], y[k]));
+    y[i] = __ddiv_rn(t, L[i * RNP_MAX_M + i]);
+  }
+  for (int i = me - 1; i >= 0; --i) {
+    double t = y[i];
+    for (int k = i + 1; k < me; ++k) t = __dsub_rn(t, __dmul_rn(L[k * RNP_MAX_M + i], x[k]));
+    x[i] = __ddiv_rn(t, L[i * RNP_MAX_M + i]);
+  }
+  for (int l = 0; l < me; ++l) alpha[b * RNP_MAX_M + l] = x[l];
+}
+
+cudaError_t launch_topm_ridge(const double* part, int nch, const double* Phi, long long cap,
+                              int M, const double* phiq, long long phiq_bstride, const int* P,
+                              int Pmax, int B, int m, double lambda, double* dist,
+                              double* alpha, int* idx, int* meff, int* esc_count, int* fail,
+                              const int* gate, cudaStream_t st) {
+  (void)Pmax;
+  count_launches(1);
+  k_topm_ridge<<<B, 256, 0, st>>>(part, nch, Phi, cap, M, phiq, phiq_bstride, P, m, lambda,
+                                  dist, alpha, idx, meff, esc_count, fail, gate);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Update of Eq. 3 with the max-norm of Eq. 5 fused in.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void block_max_to(unsigned long long* dst, double v) {
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    const double w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x = red[0];
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) x = red[k] > x ? red[k] : x;
+    atomicMax(dst, (unsigned long long)__double_as_longlong(x));
+  }
+}
+
+__global__ void __launch_bounds__(256) k_update(const double* g, long long g_bstride,
+                                                const double* Y, long long cap, long long d,
+                                                const double* alpha, const int* idx,
+                                                const int* meff, double* out,
+                                                long long out_bstride, unsigned long long* err,
+                                                long long err_bstride, int* nonfinite,
+                                                const int* gate) {
+  const int b = blockIdx.y;
+  if (gate && !gate[b]) return;
+  const int me = meff[b];
+  __shared__ double a[RNP_MAX_M];
+  __shared__ const double* Yl[RNP_MAX_M];
+  if (threadIdx.x < me) {
+    a[threadIdx.x] = alpha[b * RNP_MAX_M + threadIdx.x];
+    Yl[threadIdx.x] = Y + ((long long)b * cap + idx[b * RNP_MAX_M + threadIdx.x]) * d;
+  }
+  __syncthreads();
+  const double* gb = g ? g + (long long)b * g_bstride : nullptr;
+  double* ob = out + (long long)b * out_bstride;
+  double emax = 0.0;
+  bool bad = false;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < d;
+       j += (long long)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int l = 0; l < me; ++l) acc = __dadd_rn(acc, __dmul_rn(a[l], Yl[l][j]));
+    const double v = gb ? __dadd_rn(gb[j], acc) : acc;
+    if (err) {
+      const double e = fabs(v - ob[j]);
+      emax = e > emax ? e : emax;
+    }
+    bad |= !isfinite(v);
+    ob[j] = v;
+  }
+  if (bad) atomicExch(nonfinite, 1);
+  if (err) block_max_to(err + (long long)b * err_bstride, emax);
+}
+
+__global__ void __launch_bounds__(256) k_update_para(const double* g, long long g_bstride,
+                                                     const double* Yv, long long yv_bstride,
+                                                     long long d, double* out,
+                                                     long long out_bstride,
+                                                     unsigned long long* err,
+                                                     long long err_bstride, int* nonfinite,
+                                                     const int* gate) {
+  const int b = blockIdx.y;
+  if (gate && !gate[b]) return;
+  const double* gb = g + (long long)b * g_bstride;
+  const double* yb = Yv + (long long)b * yv_bstride;
+  double* ob = out + (long long)b * out_bstride;
+  double emax = 0.0;
+  bool bad = false;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < d;
+       j += (long long)gridDim.x * blockDim.x) {
+    const double v = __dadd_rn(gb[j], yb[j]);
+    if (err) {
+      const double e = fabs(v - ob[j]);
+      emax = e > emax ? e : emax;
+    }
+    bad |= !isfinite(v);
+    ob[j] = v;
+  }
+  if (bad) atomicExch(nonfinite, 1);
+  if (err) block_max_to(err + (long long)b * err_bstride, emax);
+}
+
+static dim3 update_grid(long long d, int B) {
+  long long bx = (d + 256 * 4 - 1) / (256 * 4);
+  if (bx > 152) bx = 152;
+  if (bx < 1) bx = 1;
+  return dim3((unsigned)bx, B);
+}
+
+cudaError_t launch_update(const double* g, long long g_bstride, const double* Y,
+                          long long cap, long long d, const double* alpha, const int* idx,
+                          const int* meff, double* out, long long out_bstride,
+                          unsigned long long* err, long long err_bstride, int* nonfinite,
+                          int B, const int* gate, cudaStream_t st) {
+  count_launches(1);
+  k_update<<<update_grid(d, B), 256, 0, st>>>(g, g_bstride, Y, cap, d, alpha, idx, meff, out,
+                                              out_bstride, err, err_bstride, nonfinite, gate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_para(const double* g, long long g_bstride, const double* Yv,
+                               long long yv_bstride, long long d, double* out,
+                               long long out_bstride, unsigned long long* err,
+                               long long err_bstride, int* nonfinite, int B, const int* gate,
+                               cudaStream_t st) {
+  count_launches(1);
+  k_update_para<<<update_grid(d, B), 256, 0, st>>>(g, g_bstride, Yv, yv_bstride, d, out,
+                                                   out_bstride, err, err_bstride, nonfinite,
+                                                   gate);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Dataset append (Eq. 6) and row copies
+// ---------------------------------------------------------------------------
+__global__ void k_append(const double* U, long long u_bstride, const double* Fv,
+                         const double* Gc, long long n_bstride, double* Yv, double* Sds,
+                         double* Yds, long long cap, const double* c, const double* r,
+                         AppendItems it, bool randnet, long long n, long long d) {
+  const long long tot = (long long)it.n * d;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int w = (int)(t / d);
+    const long long e = t - (long long)w * d;
+    const int b = it.b[w], j = it.j[w];
+    const long long ns = (long long)b * n_bstride + (long long)j * d + e;
+    const double y = __dsub_rn(Fv[ns], Gc[ns]);
+    Yv[ns] = y;
+    if (randnet) {
+      const long long ds = ((long long)b * cap + it.p[w]) * d + e;
+      Yds[ds] = y;
+      const int q = (int)(e / n);
+      const double u = U[(long long)b * u_bstride + (long long)j * d + e];
+      Sds[ds] = __ddiv_rn(__dsub_rn(u, c[b * 3 + q]), r[b * 3 + q]);
+    }
+  }
+}
+
+cudaError_t launch_append(const Geom& g, const double* U, long long u_bstride, const double* Fv,
+                          const double* Gc, long long n_bstride, double* Yv, double* Sds,
+                          double* Yds, long long cap, const double* c, const double* r,
+                          const AppendItems& it, bool randnet, cudaStream_t st) {
+  if (it.n <= 0) return cudaSuccess;
+  count_launches(1);
+  k_append<<<grid_cap((long long)it.n * g.d, 256), 256, 0, st>>>(
+      U, u_bstride, Fv, Gc, n_bstride, Yv, Sds, Yds, cap, c, r, it, randnet, g.n, g.d);
+  return cudaGetLastError();
+}
+
+__global__ void k_copy_phi(const double* src, long long src_bstride, double* dst,
+                           long long cap, int M, AppendItems it) {
+  const long long tot = (long long)it.n * M;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int w = (int)(t / M);
+    const int k = (int)(t - (long long)w * M);
+    const int b = it.b[w];
+    dst[((long long)b * cap + it.p[w]) * M + k] =
+        src[(long long)b * src_bstride + (long long)it.j[w] * M + k];
+  }
+}
+
+cudaError_t launch_copy_phi(const double* src, long long src_bstride, double* dst,
+                            long long cap, int M, const AppendItems& it, cudaStream_t st) {
+  if (it.n <= 0) return cudaSuccess;
+  count_launches(1);
+  k_copy_phi<<<grid_cap((long long)it.n * M, 256), 256, 0, st>>>(src, src_bstride, dst, cap, M,
+                                                                it);
+  return cudaGetLastError();
+}
+
+__global__ void k_copy_rows(const double* src, const long long* src_off, double* dst,
+                            const long long* dst_off, long long d, int rows) {
+  const long long tot = (long long)rows * d;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int w = (int)(t / d);
+    const long long e = t - (long long)w * d;
+    dst[dst_off[w] + e] = src[src_off[w] + e];
+  }
+}
+
+cudaError_t launch_copy_rows(const double* src, const long long* src_off, double* dst,
+                             const long long* dst_off, long long d, int rows, cudaStream_t st) {
+  if (rows <= 0) return cudaSuccess;
+  count_launches(1);
+  k_copy_rows<<<grid_cap((long long)rows * d, 256), 256, 0, st>>>(src, src_off, dst, dst_off, d,
+                                                                 rows);
+  return cudaGetLastError();
+}
+
+}  // namespace rnp

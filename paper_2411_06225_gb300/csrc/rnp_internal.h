@@ -1,0 +1,189 @@
+// rnp_internal.h -- shared declarations of librnp's kernels and launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rnp.h"
+
+namespace rnp {
+
+// Number of kernels this library has launched (all contexts, all threads).
+long long launches_total();
+void count_launches(long long n);
+
+// Kernel-level PDE ids: the heat operator is split by dimension so that the
+// stencil's dimensionality is a compile-time constant.
+enum KPde {
+  KP_BURGERS = 0, KP_ADVECT = 1, KP_HEAT1 = 2, KP_HEAT2 = 3, KP_HEAT3 = 4,
+  KP_DIFFREACT = 5, KP_BRUSS2 = 6, KP_BRUSS3 = 7, KP_SWE = 8, KP_COUNT = 9
+};
+
+enum Scheme { SCHEME_EULER = 0, SCHEME_RK4 = 1 };
+
+// Geometry of one state vector.
+struct Geom {
+  int kp;          // KPde
+  int nx, ny, nz;
+  int ncomp;
+  int dims;
+  long long n;     // cells per component
+  long long d;     // ncomp * n
+  int outer;       // extent of the axis split across a cluster (x/y/z for 1/2/3D)
+  long long plane; // cells per outer index
+};
+
+// PDE constants, precomputed on the host in FP64 exactly as the plain
+// serial formulas use them (coefficients, 1/h^2, 1/(2h), 1/h).
+struct Coef {
+  double k[12];
+};
+
+// Work-item description of a stencil launch: item w reads the state at
+// in + off(src, w) and writes out + off(dst, w) (and out2 + off(dst2, w)
+// when out2 != nullptr), where off(x, w) = x_off[w] if the table is given,
+// else x_base + w * x_stride.  gate (optional) skips items with
+// gate[w] == 0.
+struct Items {
+  const long long* src_off; long long src_base, src_stride;
+  const long long* dst_off; long long dst_base, dst_stride;
+  const long long* dst2_off; long long dst2_base, dst2_stride;
+  const int* gate;
+  int n;
+};
+
+// Row offsets of the feature / scaling kernels: table or affine.
+struct Rows {
+  const long long* off; long long base, stride;
+};
+
+#ifdef __CUDACC__
+__host__ __device__ __forceinline__ long long item_off(const long long* tab,
+                                                       long long base,
+                                                       long long stride, int w) {
+  return tab ? tab[w] : base + (long long)w * stride;
+}
+#endif
+
+struct StencilCfg {
+  int cluster;   // CTAs per slice
+  int threads;   // threads per CTA
+  int R;         // cells per thread
+};
+
+Geom make_geom(const rnp_problem& p);
+Coef make_coef(const rnp_problem& p, const Geom& g);
+
+// Choose a fused-stencil configuration.  latency = true favours many SMs per
+// item (sequential sweep), false favours throughput (many items).
+bool pick_stencil(const Geom& g, bool fp32, int nitems, bool latency,
+                  int want_cluster, int want_threads, StencilCfg* out,
+                  char* why, int why_len);
+
+// Fused stencil: every item advances `steps` RK4/Euler steps of size dt
+// inside one launch, the slice resident in the cluster's shared memory.
+cudaError_t launch_stencil_fused(const Geom& g, const Coef& c, bool fp32,
+                                 int scheme, int steps, double dt,
+                                 const double* in, double* out, double* out2,
+                                 const Items& it, const StencilCfg& cfg,
+                                 cudaStream_t st);
+
+// Plain stencil: one launch per Runge-Kutta stage over global memory.
+// work must hold 4 * n_items * d doubles.
+cudaError_t launch_stencil_plain(const Geom& g, const Coef& c, int scheme,
+                                 int steps, double dt, const double* in,
+                                 double* out, double* out2, const Items& it,
+                                 double* work, cudaStream_t st);
+
+// ---------------- RandNet kernels (randnet.cu) -----------------------------
+
+cudaError_t launch_weights(uint64_t seed, int M, long long d, double* A,
+                           double* zeta, float* A32, uint16_t* Abf16,
+                           float* zeta32, cudaStream_t st);
+
+// Per-member, per-species min/max over `nstates` consecutive states starting
+// at U + b * bstride, then c = (max + min) / 2, r = (max - min) / 2 (r = 1
+// when 0), written to c[b*3 + q], r[b*3 + q].  none = identity scaling.
+// nonfinite (optional) is set when a scanned value is NaN or Inf.
+cudaError_t launch_scaling(const Geom& g, const double* U, long long bstride,
+                           int nstates, int B, bool none, double* c, double* r,
+                           double* work, int* nonfinite, cudaStream_t st);
+
+// Rows r = 0..R-1: S[dst_off[r]..] = (U[src_off[r]..] - c[b]) / r[b]
+// with b = row_b[r].
+cudaError_t launch_scale_rows(const Geom& g, const double* U, Rows src,
+                              const int* row_b, int row_b_div,
+                              const double* c, const double* r, double* S,
+                              Rows dst, int R, const int* gate, cudaStream_t st);
+
+// Random features phi = ReLU(A s + zeta) of R scaled rows S + s_off[r],
+// written to phi + phi_off[r] (FP64).  part must hold R * M * nchunks.
+cudaError_t launch_features64(const double* A, const double* zeta, int M,
+                              long long d, const double* S, Rows s_rows, int R,
+                              double* phi, Rows phi_rows, double* part,
+                              const int* gate, cudaStream_t st);
+int features_chunks(long long d);
+
+// Squared distances of the scaled query q[b] to the P[b] stored rows of
+// member b (dataset rows at S + b * cap * d), partial over d-chunks.
+cudaError_t launch_nn_partial(const double* q, const double* S, long long cap,
+                              long long d, const int* P, int Pmax, int B,
+                              double* part, const int* gate, cudaStream_t st);
+int nn_chunks(long long d);
+
+// Per member: finish distances, select the m nearest (ties -> lower index),
+// build the dual ridge system from the stored features and phi_q, solve by
+// Cholesky (lambda x10 on a non-positive pivot, at most 4 times) and write
+// alpha[b*RNP_MAX_M + l], idx[b*RNP_MAX_M + l], meff[b].
+cudaError_t launch_topm_ridge(const double* part, int nch, const double* Phi,
+                              long long cap, int M, const double* phiq,
+                              long long phiq_bstride, const int* P, int Pmax,
+                              int B, int m, double lambda,
+                              double* dist, double* alpha, int* idx, int* meff,
+                              int* esc_count, int* fail, const int* gate,
+                              cudaStream_t st);
+
+// out[b] = g[b] + sum_l alpha_l Y[b][idx_l]  (g may be null: out = sum).
+// If err != null: err[b] = max |out_new - out_old| over the state (the old
+// value is read before it is overwritten), and nonfinite is set on NaN/Inf.
+cudaError_t launch_update(const double* g, long long g_bstride,
+                          const double* Y, long long cap, long long d,
+                          const double* alpha, const int* idx, const int* meff,
+                          double* out, long long out_bstride,
+                          unsigned long long* err, long long err_bstride,
+                          int* nonfinite, int B, const int* gate,
+                          cudaStream_t st);
+
+// Parareal (Eq. 4) update: out[b] = g[b] + Yv[b]; err / nonfinite as above.
+cudaError_t launch_update_para(const double* g, long long g_bstride,
+                               const double* Yv, long long yv_bstride,
+                               long long d, double* out, long long out_bstride,
+                               unsigned long long* err, long long err_bstride,
+                               int* nonfinite, int B, const int* gate,
+                               cudaStream_t st);
+
+// Dataset append for item w = (b, j, p): y = F[b][j] - G[b][j] is written to
+// Yv[b][j] and (randnet) to Yds[b][p]; the scaled start U[b][j] to Sds[b][p].
+struct AppendItems {
+  const int* b;
+  const int* j;
+  const int* p;
+  int n;
+};
+cudaError_t launch_append(const Geom& g, const double* U, long long u_bstride,
+                          const double* Fv, const double* Gc, long long n_bstride,
+                          double* Yv, double* Sds, double* Yds, long long cap,
+                          const double* c, const double* r,
+                          const AppendItems& it, bool randnet, cudaStream_t st);
+
+// Copy feature rows: dst[b][p] = src[b][j] for each append item.
+cudaError_t launch_copy_phi(const double* src, long long src_bstride,
+                            double* dst, long long cap, int M,
+                            const AppendItems& it, cudaStream_t st);
+
+// Element-wise copy of `rows` rows of length d with per-row offsets.
+cudaError_t launch_copy_rows(const double* src, const long long* src_off,
+                             double* dst, const long long* dst_off, long long d,
+                             int rows, cudaStream_t st);
+
+}  // namespace rnp

@@ -1,0 +1,311 @@
+// stencil.cu -- fine (F, classic RK4) and coarse (G, forward Euler or RK4)
+// propagators of Sec. 2 over the periodic finite-difference right-hand sides
+// h(u) of Eq. 1 (Sec. 5.1 Burgers, Sec. 5.2 diffusion-reaction, App. E
+// Brusselator, Sec. 5.3 shallow water, plus heat and advection operators).
+//
+// Fused path: one launch advances every work item (a slice start, or a
+// batch member in the coarse sweep) through all of its steps.  Each item is
+// owned by a thread-block cluster; the state is split along the outermost
+// axis, each CTA keeps its block of the Runge-Kutta stage input in shared
+// memory (double-buffered) and the step state u and stage accumulator in
+// registers.  Neighbour planes across a CTA boundary are read straight from
+// the neighbouring CTA's shared memory (distributed shared memory); one
+// cluster barrier separates consecutive stages.  HBM is touched only to
+// load the start state and store the end state.
+//
+// Plain path: one launch per Runge-Kutta stage over global memory.
+//
+// FP64 variants evaluate every expression with explicitly rounded
+// operations (no contraction), in the same order as the plain serial
+// formulas, so F and G are bit-identical to a serial FP64 evaluation.  FP32
+// variants let the compiler contract multiply-adds.
+#include <cstdio>
+#include <cstring>
+
+#include "stencil_impl.cuh"
+
+namespace rnp {
+
+__global__ void k_plain_load(const double* in, const Items it, long long d, double* U,
+                             double* W) {
+  const long long tot = (long long)it.n * d;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int item = (int)(t / d);
+    if (it.gate && !it.gate[item]) continue;
+    const double v = in[item_off(it.src_off, it.src_base, it.src_stride, item) +
+                        (t - (long long)item * d)];
+    U[t] = v;
+    W[t] = v;
+  }
+}
+
+__global__ void k_plain_store(const double* U, const Items it, long long d, double* out,
+                              double* out2) {
+  const long long tot = (long long)it.n * d;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int item = (int)(t / d);
+    if (it.gate && !it.gate[item]) continue;
+    const long long e = t - (long long)item * d;
+    out[item_off(it.dst_off, it.dst_base, it.dst_stride, item) + e] = U[t];
+    if (out2) out2[item_off(it.dst2_off, it.dst2_base, it.dst2_stride, item) + e] = U[t];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+Geom make_geom(const rnp_problem& p) {
+  Geom g;
+  g.nx = p.nx; g.ny = p.ny; g.nz = p.nz;
+  g.n = (long long)p.nx * p.ny * p.nz;
+  switch (p.pde) {
+    case RNP_BURGERS1D: g.kp = KP_BURGERS; g.ncomp = 1; g.dims = 1; break;
+    case RNP_ADVECT1D: g.kp = KP_ADVECT; g.ncomp = 1; g.dims = 1; break;
+    case RNP_HEAT:
+      g.ncomp = 1;
+      g.dims = p.nz > 1 ? 3 : (p.ny > 1 ? 2 : 1);
+      g.kp = g.dims == 1 ? KP_HEAT1 : (g.dims == 2 ? KP_HEAT2 : KP_HEAT3);
+      break;
+    case RNP_DIFFREACT2D: g.kp = KP_DIFFREACT; g.ncomp = 2; g.dims = 2; break;
+    case RNP_BRUSS2D: g.kp = KP_BRUSS2; g.ncomp = 2; g.dims = 2; break;
+    case RNP_BRUSS3D: g.kp = KP_BRUSS3; g.ncomp = 2; g.dims = 3; break;
+    case RNP_SWE2D: g.kp = KP_SWE; g.ncomp = 3; g.dims = 2; break;
+    default: g.kp = -1; g.ncomp = 1; g.dims = 1;
+  }
+  g.d = g.n * g.ncomp;
+  if (g.dims == 1) { g.outer = 1; g.plane = p.nx; }
+  else if (g.dims == 2) { g.outer = p.ny; g.plane = p.nx; }
+  else { g.outer = p.nz; g.plane = (long long)p.nx * p.ny; }
+  return g;
+}
+
+Coef make_coef(const rnp_problem& p, const Geom& g) {
+  Coef c;
+  memset(&c, 0, sizeof(c));
+  const double hx = p.lx / p.nx, hy = p.ly / p.ny, hz = p.lz / p.nz;
+  const double ix2 = 1.0 / (hx * hx), iy2 = 1.0 / (hy * hy), iz2 = 1.0 / (hz * hz);
+  const double* P = p.param;
+  switch (g.kp) {
+    case KP_BURGERS: c.k[0] = P[0]; c.k[1] = ix2; c.k[2] = 0.5 / hx; break;
+    case KP_ADVECT: c.k[0] = P[0]; c.k[1] = 0.5 / hx; break;
+    case KP_HEAT1: case KP_HEAT2: case KP_HEAT3:
+      c.k[0] = P[0]; c.k[1] = ix2; c.k[2] = iy2; c.k[3] = iz2; break;
+    case KP_DIFFREACT:
+      c.k[0] = P[0]; c.k[1] = P[1]; c.k[2] = P[2]; c.k[3] = ix2; c.k[4] = iy2; break;
+    case KP_BRUSS2: case KP_BRUSS3:
+      c.k[0] = P[0]; c.k[1] = P[1]; c.k[2] = P[2]; c.k[3] = P[3];
+      c.k[4] = 1.0 + P[1]; c.k[5] = ix2; c.k[6] = iy2; c.k[7] = iz2; break;
+    case KP_SWE:
+      c.k[0] = P[0]; c.k[1] = 0.5 * P[0]; c.k[2] = 1.0 / hx; c.k[3] = 1.0 / hy; break;
+  }
+  return c;
+}
+
+static FusedFn fused_fn(int kp, bool fp32, int R) {
+  switch (kp) {
+    case KP_BURGERS: return fused_fn_burgers(fp32, R);
+    case KP_ADVECT: return fused_fn_advect(fp32, R);
+    case KP_HEAT1: return fused_fn_heat1(fp32, R);
+    case KP_HEAT2: return fused_fn_heat2(fp32, R);
+    case KP_HEAT3: return fused_fn_heat3(fp32, R);
+    case KP_DIFFREACT: return fused_fn_diffreact(fp32, R);
+    case KP_BRUSS2: return fused_fn_bruss2(fp32, R);
+    case KP_BRUSS3: return fused_fn_bruss3(fp32, R);
+    case KP_SWE: return fused_fn_swe(fp32, R);
+  }
+  return nullptr;
+}
+
+static const int kRs[] = {1, 2, 4, 8, 16};
+static const int kMaxSmem = 220 * 1024;
+
+static int round_R(long long cells_per_thread) {
+  for (int R : kRs)
+    if (R >= cells_per_thread) return R;
+  return -1;
+}
+
+static bool try_cfg(const Geom& g, bool fp32, int CS, int threads, int nitems,
+                    StencilCfg* out) {
+  if (g.outer % CS) return false;
+  if (g.dims == 1 && CS != 1) return false;
+  const long long ncell = (long long)(g.outer / CS) * g.plane;
+  const size_t es = fp32 ? 4 : 8;
+  const long long smem = 2LL * g.ncomp * ncell * es;
+  if (smem > kMaxSmem) return false;
+  if (threads <= 0) {
+    // enough threads that every thread owns <= 8 (FP32) / 4 (FP64) points
+    const int target = fp32 ? 8 : 4;
+    long long t = (ncell + target - 1) / target;
+    t = ((t + 31) / 32) * 32;
+    if (t < 64) t = 64;
+    if (t > 512) t = 512;
+    threads = (int)t;
+  }
+  const int R = round_R((ncell + threads - 1) / threads);
+  if (R < 0) return false;
+  FusedFn fn = fused_fn(g.kp, fp32, R);
+  if (!fn) return false;
+  if (cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (CS > 8 &&
+      cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                           1) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaLaunchConfig_t lc = {};
+  cudaLaunchAttribute at[1];
+  lc.gridDim = dim3(CS * (nitems > 0 ? nitems : 1));
+  lc.blockDim = dim3(threads);
+  lc.dynamicSmemBytes = (size_t)smem;
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CS;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, (const void*)fn, &lc) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (nclusters < 1) return false;
+  out->cluster = CS;
+  out->threads = threads;
+  out->R = R;
+  return true;
+}
+
+bool pick_stencil(const Geom& g, bool fp32, int nitems, bool latency,
+                  int want_cluster, int want_threads, StencilCfg* out, char* why,
+                  int why_len) {
+  if (want_cluster > 0) {
+    if (try_cfg(g, fp32, want_cluster, want_threads, nitems, out)) return true;
+    snprintf(why, why_len, "stencil configuration cluster=%d threads=%d is not launchable",
+             want_cluster, want_threads);
+    return false;
+  }
+  const int cands[] = {1, 2, 4, 8, 16};
+  // smallest cluster that fits; for latency prefer up to 8 CTAs per item
+  int best = -1;
+  for (int CS : cands) {
+    StencilCfg c;
+    if (!try_cfg(g, fp32, CS, want_threads, nitems, &c)) continue;
+    if (best < 0) { *out = c; best = CS; if (!latency) break; }
+    else if (latency && CS <= 8) { *out = c; best = CS; }
+  }
+  if (best < 0) {
+    snprintf(why, why_len,
+             "state of %lld unknowns does not fit the shared memory of a 16-CTA cluster",
+             (long long)g.d);
+    return false;
+  }
+  // throughput: grow the cluster while the grid is below one CTA per SM
+  if (!latency) {
+    int sms = 152;
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    while (out->cluster < 8 && (long long)nitems * out->cluster * 2 <= sms) {
+      StencilCfg c;
+      if (!try_cfg(g, fp32, out->cluster * 2, want_threads, nitems, &c)) break;
+      *out = c;
+    }
+  }
+  return true;
+}
+
+cudaError_t launch_stencil_fused(const Geom& g, const Coef& c, bool fp32, int scheme,
+                                 int steps, double dt, const double* in, double* out,
+                                 double* out2, const Items& it, const StencilCfg& cfg,
+                                 cudaStream_t st) {
+  if (it.n <= 0 || steps <= 0) return cudaSuccess;
+  FusedFn fn = fused_fn(g.kp, fp32, cfg.R);
+  if (!fn) return cudaErrorInvalidValue;
+  FusedParams P;
+  P.in = in; P.out = out; P.out2 = out2;
+  P.it = it;
+  P.nx = g.nx; P.ny = g.ny; P.n = g.n; P.outer = g.outer; P.plane = (int)g.plane;
+  P.cluster = cfg.cluster; P.steps = steps; P.scheme = scheme;
+  P.dt = dt; P.h2 = dt / 2.0; P.h6 = dt / 6.0;
+  P.coef = c;
+  const long long ncell = (long long)(g.outer / cfg.cluster) * g.plane;
+  const size_t smem = 2 * (size_t)g.ncomp * ncell * (fp32 ? 4 : 8);
+  cudaLaunchConfig_t lc = {};
+  cudaLaunchAttribute at[1];
+  lc.gridDim = dim3(cfg.cluster * it.n);
+  lc.blockDim = dim3(cfg.threads);
+  lc.dynamicSmemBytes = smem;
+  lc.stream = st;
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cfg.cluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  count_launches(1);
+  return cudaLaunchKernelEx(&lc, fn, P);
+}
+
+static PlainFn plain_fn(int kp) {
+  switch (kp) {
+    case KP_BURGERS: return plain_fn_burgers();
+    case KP_ADVECT: return plain_fn_advect();
+    case KP_HEAT1: return plain_fn_heat1();
+    case KP_HEAT2: return plain_fn_heat2();
+    case KP_HEAT3: return plain_fn_heat3();
+    case KP_DIFFREACT: return plain_fn_diffreact();
+    case KP_BRUSS2: return plain_fn_bruss2();
+    case KP_BRUSS3: return plain_fn_bruss3();
+    case KP_SWE: return plain_fn_swe();
+  }
+  return nullptr;
+}
+
+static int grid_for(long long tot, int threads) {
+  long long b = (tot + threads - 1) / threads;
+  if (b > 152LL * 16) b = 152LL * 16;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+cudaError_t launch_stencil_plain(const Geom& g, const Coef& c, int scheme, int steps,
+                                 double dt, const double* in, double* out, double* out2,
+                                 const Items& it, double* work, cudaStream_t st) {
+  if (it.n <= 0 || steps <= 0) return cudaSuccess;
+  PlainFn fn = plain_fn(g.kp);
+  if (!fn) return cudaErrorInvalidValue;
+  const long long tot = (long long)it.n * g.d;
+  double* U = work;
+  double* Acc = work + tot;
+  double* Wb[2] = {work + 2 * tot, work + 3 * tot};
+  count_launches(1);
+  k_plain_load<<<grid_for(tot, 256), 256, 0, st>>>(in, it, g.d, U, Wb[0]);
+  PlainParams P;
+  P.U = U; P.Acc = Acc; P.gate = it.gate; P.nitems = it.n;
+  P.nx = g.nx; P.ny = g.ny; P.nz = g.nz; P.n = g.n; P.d = g.d;
+  P.scheme = scheme; P.dt = dt; P.h2 = dt / 2.0; P.h6 = dt / 6.0; P.coef = c;
+  const int S = scheme == SCHEME_RK4 ? 4 : 1;
+  const long long cells = (long long)it.n * g.n;
+  int cur = 0;
+  for (int step = 0; step < steps; ++step)
+    for (int s = 0; s < S; ++s) {
+      P.Wc = Wb[cur];
+      P.Wn = Wb[cur ^ 1];
+      P.stage = s;
+      count_launches(1);
+      fn<<<grid_for(cells, 256), 256, 0, st>>>(P);
+      cur ^= 1;
+    }
+  count_launches(1);
+  k_plain_store<<<grid_for(tot, 256), 256, 0, st>>>(U, it, g.d, out, out2);
+  return cudaGetLastError();
+}
+
+}  // namespace rnp
