@@ -130,6 +130,7 @@ typedef struct {
   double t_sweep_ms;      /* device time in the sequential sweeps           */
   double t_fit_ms;        /* device time appending pairs and features       */
   double t_total_ms;      /* wall time of the call                          */
+  long long kernel_launches; /* kernels this call launched                   */
   int K_each[RNP_MAX_BATCH];  /* per-member iterations                      */
 } rnp_stats;
 
