@@ -148,8 +148,19 @@ static bool try_cfg(const Geom& g, bool fp32, int CS, int threads, int nitems,
   if (R < 0) return false;
   FusedFn fn = fused_fn(g.kp, fp32, R);
   if (!fn) return false;
+  // The limit is a per-function attribute shared by every configuration that
+  // maps to this instantiation, so it is raised to the device maximum once
+  // rather than set to this configuration's size.
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (smem > optin) return false;
   if (cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem) != cudaSuccess) {
+                           optin) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
