@@ -68,7 +68,8 @@ __host__ __device__ __forceinline__ long long item_off(const long long* tab,
 struct StencilCfg {
   int cluster;   // CTAs per slice
   int threads;   // threads per CTA
-  int R;         // cells per thread
+  int R;         // cells per thread (FP64 kernel)
+  int px, rs;    // x-points and outer rows per thread (mixed kernel)
 };
 
 Geom make_geom(const rnp_problem& p);

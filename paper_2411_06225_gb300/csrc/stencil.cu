@@ -118,6 +118,21 @@ static FusedFn fused_fn(int kp, bool fp32, int R) {
   return nullptr;
 }
 
+static FusedFn mixed_fn(int kp, int PX, int RS) {
+  switch (kp) {
+    case KP_BURGERS: return mixed_fn_burgers(PX, RS);
+    case KP_ADVECT: return mixed_fn_advect(PX, RS);
+    case KP_HEAT1: return mixed_fn_heat1(PX, RS);
+    case KP_HEAT2: return mixed_fn_heat2(PX, RS);
+    case KP_HEAT3: return mixed_fn_heat3(PX, RS);
+    case KP_DIFFREACT: return mixed_fn_diffreact(PX, RS);
+    case KP_BRUSS2: return mixed_fn_bruss2(PX, RS);
+    case KP_BRUSS3: return mixed_fn_bruss3(PX, RS);
+    case KP_SWE: return mixed_fn_swe(PX, RS);
+  }
+  return nullptr;
+}
+
 static const int kRs[] = {1, 2, 4, 8, 16};
 static const int kMaxSmem = 220 * 1024;
 
@@ -127,30 +142,13 @@ static int round_R(long long cells_per_thread) {
   return -1;
 }
 
-static bool try_cfg(const Geom& g, bool fp32, int CS, int threads, int nitems,
-                    StencilCfg* out) {
-  if (g.outer % CS) return false;
-  if (g.dims == 1 && CS != 1) return false;
+static size_t smem_bytes(const Geom& g, bool fp32, int CS) {
   const long long ncell = (long long)(g.outer / CS) * g.plane;
-  const size_t es = fp32 ? 4 : 8;
-  const long long smem = 2LL * g.ncomp * ncell * es;
-  if (smem > kMaxSmem) return false;
-  if (threads <= 0) {
-    // enough threads that every thread owns <= 8 (FP32) / 4 (FP64) points
-    const int target = fp32 ? 8 : 4;
-    long long t = (ncell + target - 1) / target;
-    t = ((t + 31) / 32) * 32;
-    if (t < 64) t = 64;
-    if (t > 512) t = 512;
-    threads = (int)t;
-  }
-  const int R = round_R((ncell + threads - 1) / threads);
-  if (R < 0) return false;
-  FusedFn fn = fused_fn(g.kp, fp32, R);
-  if (!fn) return false;
-  // The limit is a per-function attribute shared by every configuration that
-  // maps to this instantiation, so it is raised to the device maximum once
-  // rather than set to this configuration's size.
+  // FP64 kernel: two stage buffers; mixed kernel: two buffers + the low words
+  return fp32 ? 3 * (size_t)g.ncomp * ncell * 4 : 2 * (size_t)g.ncomp * ncell * 8;
+}
+
+static bool launchable(FusedFn fn, int CS, int threads, size_t smem, int nitems) {
   int dev = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
@@ -158,7 +156,10 @@ static bool try_cfg(const Geom& g, bool fp32, int CS, int threads, int nitems,
     cudaGetLastError();
     return false;
   }
-  if (smem > optin) return false;
+  if ((long long)smem > optin) return false;
+  // The limit is a per-function attribute shared by every configuration that
+  // maps to this instantiation, so it is raised to the device maximum once
+  // rather than set to this configuration's size.
   if (cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            optin) != cudaSuccess) {
     cudaGetLastError();
@@ -174,7 +175,7 @@ static bool try_cfg(const Geom& g, bool fp32, int CS, int threads, int nitems,
   cudaLaunchAttribute at[1];
   lc.gridDim = dim3(CS * (nitems > 0 ? nitems : 1));
   lc.blockDim = dim3(threads);
-  lc.dynamicSmemBytes = (size_t)smem;
+  lc.dynamicSmemBytes = smem;
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = CS;
   at[0].val.clusterDim.y = 1;
@@ -186,26 +187,93 @@ static bool try_cfg(const Geom& g, bool fp32, int CS, int threads, int nitems,
     cudaGetLastError();
     return false;
   }
-  if (nclusters < 1) return false;
+  return nclusters >= 1;
+}
+
+static bool try_cfg(const Geom& g, bool fp32, int CS, int threads, int nitems,
+                    StencilCfg* out) {
+  if (g.outer % CS) return false;
+  if (g.dims == 1 && CS != 1) return false;
+  const long long nloc = g.outer / CS;
+  const long long ncell = nloc * g.plane;
+  const size_t smem = smem_bytes(g, fp32, CS);
+  if (fp32 && smem <= (size_t)kMaxSmem) {
+    // mixed kernel: PX x-points by RS rows per thread; the most threads
+    // (up to 512) whose register tile fits, or exactly `threads` if given
+    const int pxs[] = {2, 4};
+    const int rss[] = {1, 2, 4, 5, 8};
+    for (int PX : pxs) {
+      if (g.nx % PX) continue;
+      const long long tiles = g.plane / PX;
+      for (int RS : rss) {
+        if (nloc % RS) continue;
+        // register tile measured spill-free with ptxas at 512 threads
+        const int budget = (g.dims <= 2 && g.ncomp <= 2) ? 16 : 8;
+        if (RS * g.ncomp * PX > budget) continue;
+        const long long t = tiles * (nloc / RS);
+        if (t > 512 || t < 1) continue;
+        if (threads > 0 && t != threads) continue;
+        FusedFn fn = mixed_fn(g.kp, PX, RS);
+        if (!fn || !launchable(fn, CS, (int)t, smem, nitems)) continue;
+        out->cluster = CS;
+        out->threads = (int)t;
+        out->R = 0;
+        out->px = PX;
+        out->rs = RS;
+        return true;
+      }
+    }
+    return false;
+  }
+  if (fp32) return false;
+  if (smem_bytes(g, false, CS) > (size_t)kMaxSmem) return false;
+  if (threads <= 0) {
+    // enough threads that every thread owns <= 4 points
+    long long t = (ncell + 3) / 4;
+    t = ((t + 31) / 32) * 32;
+    if (t < 64) t = 64;
+    if (t > 512) t = 512;
+    threads = (int)t;
+  }
+  const int R = round_R((ncell + threads - 1) / threads);
+  if (R < 0) return false;
+  FusedFn fn = fused_fn(g.kp, false, R);
+  if (!fn || !launchable(fn, CS, threads, smem_bytes(g, false, CS), nitems)) return false;
   out->cluster = CS;
   out->threads = threads;
   out->R = R;
+  out->px = out->rs = 0;
   return true;
 }
 
-bool pick_stencil(const Geom& g, bool fp32, int nitems, bool latency,
-                  int want_cluster, int want_threads, StencilCfg* out, char* why,
-                  int why_len) {
+static bool pick_one(const Geom& g, bool fp32, int nitems, bool latency, int want_cluster,
+                     int want_threads, StencilCfg* out, char* why, int why_len);
+
+bool pick_stencil(const Geom& g, bool fp32, int nitems, bool latency, int want_cluster,
+                  int want_threads, StencilCfg* out, char* why, int why_len) {
+  // a mixed-precision context prefers an FP32 tile at any cluster size and
+  // falls back to the FP64 kernel only when no FP32 tile fits
+  if (fp32 && pick_one(g, true, nitems, latency, want_cluster, want_threads, out, why, why_len))
+    return true;
+  return pick_one(g, false, nitems, latency, want_cluster, want_threads, out, why, why_len);
+}
+
+static bool pick_one(const Geom& g, bool fp32, int nitems, bool latency, int want_cluster,
+                     int want_threads, StencilCfg* out, char* why, int why_len) {
   if (want_cluster > 0) {
     if (try_cfg(g, fp32, want_cluster, want_threads, nitems, out)) return true;
     snprintf(why, why_len, "stencil configuration cluster=%d threads=%d is not launchable",
              want_cluster, want_threads);
     return false;
   }
-  const int cands[] = {1, 2, 4, 8, 16};
-  // smallest cluster that fits; for latency prefer up to 8 CTAs per item
+  // every cluster size up to 16 that divides the split axis; the smallest
+  // that fits, or for latency the largest up to 8 (16 when nothing smaller fits)
+  int cands[16], nc = 0;
+  for (int CS = 1; CS <= 16; ++CS)
+    if (g.outer % CS == 0) cands[nc++] = CS;
   int best = -1;
-  for (int CS : cands) {
+  for (int ci = 0; ci < nc; ++ci) {
+    const int CS = cands[ci];
     StencilCfg c;
     if (!try_cfg(g, fp32, CS, want_threads, nitems, &c)) continue;
     if (best < 0) { *out = c; best = CS; if (!latency) break; }
@@ -223,10 +291,11 @@ bool pick_stencil(const Geom& g, bool fp32, int nitems, bool latency,
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess)
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    while (out->cluster < 8 && (long long)nitems * out->cluster * 2 <= sms) {
+    for (int ci = 0; ci < nc; ++ci) {
+      const int CS = cands[ci];
+      if (CS <= out->cluster || CS > 8 || (long long)nitems * CS > sms) continue;
       StencilCfg c;
-      if (!try_cfg(g, fp32, out->cluster * 2, want_threads, nitems, &c)) break;
-      *out = c;
+      if (try_cfg(g, fp32, CS, want_threads, nitems, &c)) *out = c;
     }
   }
   return true;
@@ -237,7 +306,9 @@ cudaError_t launch_stencil_fused(const Geom& g, const Coef& c, bool fp32, int sc
                                  double* out2, const Items& it, const StencilCfg& cfg,
                                  cudaStream_t st) {
   if (it.n <= 0 || steps <= 0) return cudaSuccess;
-  FusedFn fn = fused_fn(g.kp, fp32, cfg.R);
+  // a mixed-precision context uses the FP64 kernel where no FP32 tile fits
+  const bool use_mixed = fp32 && cfg.px > 0;
+  FusedFn fn = use_mixed ? mixed_fn(g.kp, cfg.px, cfg.rs) : fused_fn(g.kp, false, cfg.R);
   if (!fn) return cudaErrorInvalidValue;
   FusedParams P;
   P.in = in; P.out = out; P.out2 = out2;
@@ -246,13 +317,13 @@ cudaError_t launch_stencil_fused(const Geom& g, const Coef& c, bool fp32, int sc
   P.cluster = cfg.cluster; P.steps = steps; P.scheme = scheme;
   P.dt = dt; P.h2 = dt / 2.0; P.h6 = dt / 6.0;
   P.coef = c;
-  const long long ncell = (long long)(g.outer / cfg.cluster) * g.plane;
-  const size_t smem = 2 * (size_t)g.ncomp * ncell * (fp32 ? 4 : 8);
+  for (int i = 0; i < 12; ++i) P.kf[i] = (float)c.k[i];
+  P.fdt = (float)P.dt; P.fh2 = (float)P.h2; P.fh6 = (float)P.h6;
   cudaLaunchConfig_t lc = {};
   cudaLaunchAttribute at[1];
   lc.gridDim = dim3(cfg.cluster * it.n);
   lc.blockDim = dim3(cfg.threads);
-  lc.dynamicSmemBytes = smem;
+  lc.dynamicSmemBytes = smem_bytes(g, use_mixed, cfg.cluster);
   lc.stream = st;
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = cfg.cluster;

@@ -146,6 +146,8 @@ struct FusedParams {
   int scheme;
   double dt, h2, h6;
   Coef coef;
+  float kf[12];      // coefficients rounded to FP32 (mixed kernel)
+  float fdt, fh2, fh6;
 };
 
 template <int KP, typename T, bool EX, int R>
@@ -359,6 +361,245 @@ __global__ void k_stage_plain(const PlainParams P) {
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Mixed-precision fused kernel: FP32 arithmetic, compensated state.
+//
+// Same residency scheme as k_stencil_fused, with three differences:
+//  * the step state is an unevaluated sum u = uh + ul of two FP32 numbers;
+//    each step's increment is added with an error-free TwoSum (Knuth), so the
+//    state keeps ~48 bits over thousands of steps while every right-hand
+//    side is evaluated in FP32 (uh in registers, ul in shared memory);
+//  * thread t owns PX adjacent x-points (vector shared-memory accesses) over
+//    RS consecutive outer rows: the outer-axis neighbours come from a rolling
+//    window of registers, only the x neighbours (and y in 3D) are loaded;
+//  * the four Runge-Kutta stages are unrolled at compile time.
+// Requires nx % PX == 0 and (outer / cluster) % RS == 0.
+// ---------------------------------------------------------------------------
+template <int PX> struct VecT;
+template <> struct VecT<1> { typedef float T; };
+template <> struct VecT<2> { typedef float2 T; };
+template <> struct VecT<4> { typedef float4 T; };
+
+template <int PX>
+__device__ __forceinline__ void ld_vec(const float* p, float* v) {
+  if constexpr (PX == 1) { v[0] = p[0]; }
+  else if constexpr (PX == 2) { float2 t = *reinterpret_cast<const float2*>(p); v[0] = t.x; v[1] = t.y; }
+  else { float4 t = *reinterpret_cast<const float4*>(p); v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w; }
+}
+template <int PX>
+__device__ __forceinline__ void st_vec(float* p, const float* v) {
+  if constexpr (PX == 1) { p[0] = v[0]; }
+  else if constexpr (PX == 2) { *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]); }
+  else { *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]); }
+}
+
+// (uh, ul) += x without rounding error in the sum (TwoSum, then renormalise).
+__device__ __forceinline__ void two_sum_acc(float& uh, float& ul, float x) {
+  const float s = __fadd_rn(uh, x);
+  const float bb = __fsub_rn(s, uh);
+  const float err = __fadd_rn(__fsub_rn(uh, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+  const float l = __fadd_rn(ul, err);
+  const float h = __fadd_rn(s, l);
+  ul = __fsub_rn(l, __fsub_rn(h, s));
+  uh = h;
+}
+
+template <int KP, int PX, int RS, int STAGE>
+__device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* __restrict__ B,
+                                            float* __restrict__ Bn, const float* BP,
+                                            const float* BN, float* ulo,
+                                            float (&uh)[RS][KT<KP>::NC][PX],
+                                            float (&acc)[RS][KT<KP>::NC][PX],
+                                            int ncell, int plane, int nloc, int o0,
+                                            int rowoff, int woff, int eoff, int yn_off, int ys_off,
+                                            bool euler) {
+  const float* kk = P.kf;
+  const float dt = P.fdt, h2 = P.fh2, h6 = P.fh6;
+  constexpr int NC = KT<KP>::NC, DIMS = KT<KP>::DIMS;
+  float prv[NC][PX], cur[NC][PX], nxt[NC][PX];
+  // rolling window along the outer axis (rows o0-1, o0, o0+1, ...)
+#pragma unroll
+  for (int q = 0; q < NC; ++q) {
+    ld_vec<PX>(B + q * ncell + o0 * plane + rowoff, cur[q]);
+    if (DIMS >= 2) {
+      if (o0 > 0) ld_vec<PX>(B + q * ncell + (o0 - 1) * plane + rowoff, prv[q]);
+      else ld_vec<PX>(BP + q * ncell + (nloc - 1) * plane + rowoff, prv[q]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < RS; ++r) {
+    const int o = o0 + r;
+    const int cb = o * plane + rowoff;  // first cell of this tile row
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      if (DIMS >= 2) {
+        if (o + 1 < nloc) ld_vec<PX>(B + q * ncell + cb + plane, nxt[q]);
+        else ld_vec<PX>(BN + q * ncell + rowoff, nxt[q]);
+      }
+    }
+    float ew[NC], ee[NC];
+    float yn[NC][PX], ys[NC][PX];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      const float* Bq = B + q * ncell + o * plane;
+      ew[q] = Bq[woff];
+      ee[q] = Bq[eoff];
+      if (DIMS == 3) {
+        ld_vec<PX>(Bq + yn_off, yn[q]);
+        ld_vec<PX>(Bq + ys_off, ys[q]);
+      }
+    }
+    float wout[NC][PX];
+#pragma unroll
+    for (int p = 0; p < PX; ++p) {
+      float Cv[NC], Ev[NC], Wv[NC], Nv[NC], Sv[NC], Uv[NC], Dv[NC], k[NC];
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        Cv[q] = cur[q][p];
+        Ev[q] = (p + 1 < PX) ? cur[q][p + 1] : ee[q];
+        Wv[q] = (p > 0) ? cur[q][p - 1] : ew[q];
+        if (DIMS == 2) { Nv[q] = nxt[q][p]; Sv[q] = prv[q][p]; Uv[q] = Dv[q] = 0.f; }
+        else if (DIMS == 3) { Nv[q] = yn[q][p]; Sv[q] = ys[q][p]; Uv[q] = nxt[q][p]; Dv[q] = prv[q][p]; }
+        else { Nv[q] = Sv[q] = Uv[q] = Dv[q] = 0.f; }
+      }
+      rhs_point<KP, float, false>(Cv, Ev, Wv, Nv, Sv, Uv, Dv, kk, k);
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        float w;
+        if (euler) {
+          float l = ulo[q * ncell + cb + p];
+          two_sum_acc(uh[r][q][p], l, __fmul_rn(dt, k[q]));
+          ulo[q * ncell + cb + p] = l;
+          w = uh[r][q][p];
+        } else if (STAGE == 0) {
+          acc[r][q][p] = k[q];
+          w = uh[r][q][p] + h2 * k[q];
+        } else if (STAGE == 1) {
+          acc[r][q][p] = acc[r][q][p] + 2.f * k[q];
+          w = uh[r][q][p] + h2 * k[q];
+        } else if (STAGE == 2) {
+          acc[r][q][p] = acc[r][q][p] + 2.f * k[q];
+          w = uh[r][q][p] + dt * k[q];
+        } else {
+          const float a = acc[r][q][p] + k[q];
+          float l = ulo[q * ncell + cb + p];
+          two_sum_acc(uh[r][q][p], l, __fmul_rn(h6, a));
+          ulo[q * ncell + cb + p] = l;
+          w = uh[r][q][p];
+        }
+        wout[q][p] = w;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      st_vec<PX>(Bn + q * ncell + cb, wout[q]);
+      if (DIMS >= 2) {
+#pragma unroll
+        for (int p = 0; p < PX; ++p) { prv[q][p] = cur[q][p]; cur[q][p] = nxt[q][p]; }
+      }
+    }
+  }
+}
+
+template <int KP, int PX, int RS>
+__global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant__ FusedParams P) {
+  constexpr int NC = KT<KP>::NC, DIMS = KT<KP>::DIMS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int CS = P.cluster;
+  const int rank = CS > 1 ? (int)cg::this_cluster().block_rank() : 0;
+  const int item = blockIdx.x / CS;
+  if (item >= P.it.n) return;                // uniform over the cluster
+  if (P.it.gate && !P.it.gate[item]) return; // uniform over the cluster
+  const int plane = P.plane, nx = P.nx, ny = P.ny;
+  const int nloc = P.outer / CS;
+  const int ncell = nloc * plane;
+  float* const buf0 = reinterpret_cast<float*>(smem_raw);
+  float* const buf1 = buf0 + NC * ncell;
+  float* const ulo = buf1 + NC * ncell;
+  const float *rp0 = buf0, *rp1 = buf1, *rn0 = buf0, *rn1 = buf1;
+  if (CS > 1) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rp = (rank + CS - 1) % CS, rn = (rank + 1) % CS;
+    rp0 = cl.map_shared_rank(buf0, rp);
+    rp1 = cl.map_shared_rank(buf1, rp);
+    rn0 = cl.map_shared_rank(buf0, rn);
+    rn1 = cl.map_shared_rank(buf1, rn);
+  }
+  // tile of this thread: PX x-points at inner offset rowoff, rows o0 .. o0+RS-1
+  const int tiles = plane / PX;
+  const int ti = threadIdx.x % tiles;
+  const int o0 = (threadIdx.x / tiles) * RS;
+  const int rowoff = ti * PX;                  // offset inside the plane
+  const int x0 = rowoff % nx;
+  const int yrow = rowoff / nx;                // y index in 3D (0 otherwise)
+  const int xw = x0 == 0 ? nx - 1 : x0 - 1;
+  const int xe = x0 + PX == nx ? 0 : x0 + PX;
+  const int yn_off = (DIMS == 3 ? ((yrow + 1 == ny ? 0 : yrow + 1) * nx) : 0) + x0;
+  const int ys_off = (DIMS == 3 ? ((yrow == 0 ? ny - 1 : yrow - 1) * nx) : 0) + x0;
+  const int woff = yrow * nx + xw, eoff = yrow * nx + xe;
+
+  const long long base = (long long)rank * ncell;
+  const double* in = P.in + item_off(P.it.src_off, P.it.src_base, P.it.src_stride, item) + base;
+  float uh[RS][NC][PX], acc[RS][NC][PX];
+#pragma unroll
+  for (int r = 0; r < RS; ++r)
+#pragma unroll
+    for (int q = 0; q < NC; ++q)
+#pragma unroll
+      for (int p = 0; p < PX; ++p) {
+        const int cell = (o0 + r) * plane + rowoff + p;
+        const double v = in[q * P.n + cell];
+        const float h = (float)v;
+        uh[r][q][p] = h;
+        acc[r][q][p] = 0.f;
+        buf0[q * ncell + cell] = h;
+        ulo[q * ncell + cell] = (float)(v - (double)h);
+      }
+  if (CS > 1) cg::this_cluster().sync(); else __syncthreads();
+
+  const bool rk4 = P.scheme == SCHEME_RK4;
+  for (int step = 0; step < P.steps; ++step) {
+    if (rk4) {
+      mixed_stage<KP, PX, RS, 0>(P, buf0, buf1, rp0, rn0, ulo, uh, acc, ncell, plane, nloc, o0,
+                                 rowoff, woff, eoff, yn_off, ys_off, false);
+      if (CS > 1) cg::this_cluster().sync(); else __syncthreads();
+      mixed_stage<KP, PX, RS, 1>(P, buf1, buf0, rp1, rn1, ulo, uh, acc, ncell, plane, nloc, o0,
+                                 rowoff, woff, eoff, yn_off, ys_off, false);
+      if (CS > 1) cg::this_cluster().sync(); else __syncthreads();
+      mixed_stage<KP, PX, RS, 2>(P, buf0, buf1, rp0, rn0, ulo, uh, acc, ncell, plane, nloc, o0,
+                                 rowoff, woff, eoff, yn_off, ys_off, false);
+      if (CS > 1) cg::this_cluster().sync(); else __syncthreads();
+      mixed_stage<KP, PX, RS, 3>(P, buf1, buf0, rp1, rn1, ulo, uh, acc, ncell, plane, nloc, o0,
+                                 rowoff, woff, eoff, yn_off, ys_off, false);
+      if (CS > 1) cg::this_cluster().sync(); else __syncthreads();
+    } else {
+      // forward Euler: buffers alternate every step
+      if ((step & 1) == 0)
+        mixed_stage<KP, PX, RS, 0>(P, buf0, buf1, rp0, rn0, ulo, uh, acc, ncell, plane, nloc, o0,
+                                 rowoff, woff, eoff, yn_off, ys_off, true);
+      else
+        mixed_stage<KP, PX, RS, 0>(P, buf1, buf0, rp1, rn1, ulo, uh, acc, ncell, plane, nloc, o0,
+                                 rowoff, woff, eoff, yn_off, ys_off, true);
+      if (CS > 1) cg::this_cluster().sync(); else __syncthreads();
+    }
+  }
+  double* out = P.out + item_off(P.it.dst_off, P.it.dst_base, P.it.dst_stride, item) + base;
+  double* out2 = P.out2 ? P.out2 + item_off(P.it.dst2_off, P.it.dst2_base, P.it.dst2_stride, item) + base
+                        : nullptr;
+#pragma unroll
+  for (int r = 0; r < RS; ++r)
+#pragma unroll
+    for (int q = 0; q < NC; ++q)
+#pragma unroll
+      for (int p = 0; p < PX; ++p) {
+        const int cell = (o0 + r) * plane + rowoff + p;
+        const double v = (double)uh[r][q][p] + (double)ulo[q * ncell + cell];
+        out[q * P.n + cell] = v;
+        if (out2) out2[q * P.n + cell] = v;
+      }
+}
+
 typedef void (*FusedFn)(const FusedParams);
 typedef void (*PlainFn)(const PlainParams);
 
@@ -374,9 +615,22 @@ inline FusedFn fused_for_R(int R) {
   }
 }
 
+template <int KP, int PX>
+inline FusedFn mixed_for_RS(int RS) {
+  switch (RS) {
+    case 1: return k_stencil_mixed<KP, PX, 1>;
+    case 2: return k_stencil_mixed<KP, PX, 2>;
+    case 4: return k_stencil_mixed<KP, PX, 4>;
+    case 5: return k_stencil_mixed<KP, PX, 5>;
+    case 8: return k_stencil_mixed<KP, PX, 8>;
+    default: return nullptr;
+  }
+}
+
 // Per-PDE entry points, defined in stencil_<pde>.cu.
 #define RNP_STENCIL_DECL(NAME)                 \
   FusedFn fused_fn_##NAME(bool fp32, int R);   \
+  FusedFn mixed_fn_##NAME(int PX, int RS);     \
   PlainFn plain_fn_##NAME();
 RNP_STENCIL_DECL(burgers)
 RNP_STENCIL_DECL(advect)
@@ -392,6 +646,9 @@ RNP_STENCIL_DECL(swe)
 #define RNP_STENCIL_DEFINE(KPV, NAME)                                                \
   FusedFn fused_fn_##NAME(bool fp32, int R) {                                        \
     return fp32 ? fused_for_R<KPV, float, false>(R) : fused_for_R<KPV, double, true>(R); \
+  }                                                                                  \
+  FusedFn mixed_fn_##NAME(int PX, int RS) {                                         \
+    return PX == 2 ? mixed_for_RS<KPV, 2>(RS) : PX == 4 ? mixed_for_RS<KPV, 4>(RS) : nullptr; \
   }                                                                                  \
   PlainFn plain_fn_##NAME() { return k_stage_plain<KPV>; }
 
