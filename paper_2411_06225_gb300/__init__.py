@@ -101,7 +101,8 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    from .build import build as _build
+    """Compile librnp.so with nvcc for sm_103a (see builder.py)."""
+    from .builder import build as _build
     return _build(force=force)
 
 

@@ -1,6 +1,6 @@
 """Build librnp.so in-tree with nvcc for sm_103a (GB300).
 
-Usage: ``python -m paper_2411_06225_gb300.build [--force]``.  Translation
+Usage: ``python -m paper_2411_06225_gb300.builder [--force]``.  Translation
 units compile in parallel; a stamp of sources and flags skips up-to-date
 builds.  Nothing here needs a GPU: nvcc cross-compiles.
 """
