@@ -204,6 +204,42 @@ rnp_status rnp_get_pairs(rnp_ctx* ctx, long long* pairs);
 /* Unknowns per state. */
 long long rnp_dim(const rnp_problem* prob);
 
+/* --- allocation-free prediction (no counterpart in the paper) ----------- */
+
+/* rnp_randnet_predict for callers that cannot allocate device memory when
+ * they need a prediction: creating a context allocates, and some callers run
+ * where an allocation is not allowed or would synchronise the device (a
+ * real-time loop with a fixed memory plan, a host callback on a stream, an
+ * application that only hands out pre-allocated buffers).  This call makes
+ * the same prediction for one query without a context and calls no
+ * allocating routine: the caller passes every input and the output, and the
+ * intermediates (scaled query, features, distance partials, ridge weights)
+ * live in one fixed file-scope device array of about 6.3 MB that every GPU
+ * loading the library keeps until the process exits.
+ *   prob       : only pde, grid, M, m and lambda are read.
+ *   A, zeta    : device [M][d], [M]  random weights (e.g. rnp_get_weights).
+ *   S, Y, Phi  : device [P][d], [P][d], [P][M]  scaled inputs
+ *                ((u - c) / r per species), targets F - G, and features
+ *                ReLU(A s + zeta) of the stored pairs.
+ *   c, r       : host [3]  per-species scaling of the query.
+ *   q, out     : device [d]  query (unscaled) and prediction.
+ *   status     : device int, may be NULL; receives RNP_OK, or
+ *                RNP_ENONFINITE when the ridge system failed or the output
+ *                is not finite (out is then 0 or not finite).
+ * Limits: d <= 262144, P <= 4096, M <= 1024; larger sizes return RNP_EINVAL
+ * before any work (message in rnp_last_error(NULL)).  Work is enqueued on
+ * cuda_stream and the call returns without waiting.  The first call on a
+ * device looks up the array's device address once (with that device
+ * current); make that first call before any stream capture.  Every call on
+ * a device shares the one array: calls whose work overlaps on the GPU (other
+ * streams, other threads) race and must be serialised by the caller.     */
+rnp_status rnp_randnet_predict_noalloc(const rnp_problem* prob, const double* A,
+                                       const double* zeta, const double* S,
+                                       const double* Y, const double* Phi, int P,
+                                       const double* c, const double* r,
+                                       const double* q, double* out, int* status,
+                                       void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -138,6 +138,9 @@ def lib() -> C.CDLL:
         "rnp_reset": (C.c_int, [vp]),
         "rnp_get_pairs": (C.c_int, [vp, C.POINTER(C.c_longlong)]),
         "rnp_dim": (C.c_longlong, [C.POINTER(Problem)]),
+        "rnp_randnet_predict_noalloc": (C.c_int, [
+            C.POINTER(Problem), dp, dp, dp, dp, dp, C.c_int, C.POINTER(C.c_double),
+            C.POINTER(C.c_double), dp, dp, dp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -66,6 +66,8 @@ struct rnp_ctx {
 
 static thread_local std::string g_create_error;
 
+void rnp::set_global_error(const char* msg) { g_create_error = msg; }
+
 namespace {
 
 struct DevGuard {

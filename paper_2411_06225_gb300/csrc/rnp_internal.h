@@ -12,6 +12,9 @@ namespace rnp {
 long long launches_total();
 void count_launches(long long n);
 
+// Message returned by rnp_last_error(NULL) (calls without a context).
+void set_global_error(const char* msg);
+
 // Kernel-level PDE ids: the heat operator is split by dimension so that the
 // stencil's dimensionality is a compile-time constant.
 enum KPde {
