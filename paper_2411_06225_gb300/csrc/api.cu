@@ -38,6 +38,7 @@ struct rnp_ctx {
          *qbuf = nullptr, *phic = nullptr, *phiq = nullptr;
   double *Sds = nullptr, *Yds = nullptr, *Phi = nullptr;
   double *A = nullptr, *zeta = nullptr;
+  float *A32 = nullptr, *S32 = nullptr, *q32 = nullptr;  // mixed precision copies
   double *sc = nullptr, *sr = nullptr, *scale_work = nullptr;
   double *feat_part = nullptr, *nn_part = nullptr, *dist = nullptr, *alpha = nullptr;
   int *idx = nullptr, *meff = nullptr, *flags = nullptr;  // flags: esc, fail, nonfinite
@@ -61,6 +62,12 @@ struct rnp_ctx {
   double h_c[RNP_MAX_BATCH * 3], h_r[RNP_MAX_BATCH * 3];
 
   cudaEvent_t ev[6] = {};
+  // side stream for the coarse step of the sweep, fork/join events, and the
+  // CUDA graphs of the solve's sweep keyed by its first index
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t evf = nullptr, evj = nullptr;
+  std::vector<cudaGraphExec_t> sweep_graph;
+  std::vector<long long> sweep_graph_launches;
   std::string msg;
 };
 
@@ -144,7 +151,7 @@ void destroy_buffers(rnp_ctx* c) {
   void* bufs[] = {c->U, c->Fv, c->Gc, c->Yv, c->gbuf, c->qbuf, c->phic, c->phiq, c->Sds,
                   c->Yds, c->Phi, c->A, c->zeta, c->sc, c->sr, c->scale_work, c->feat_part,
                   c->nn_part, c->dist, c->alpha, c->idx, c->meff, c->flags, c->dP, c->err,
-                  c->plain_work, c->d_items, c->d_app, c->d_gate};
+                  c->plain_work, c->d_items, c->d_app, c->d_gate, c->A32, c->S32, c->q32};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->h_items) cudaFreeHost(c->h_items);
@@ -154,23 +161,29 @@ void destroy_buffers(rnp_ctx* c) {
   if (c->h_flags) cudaFreeHost(c->h_flags);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
+  if (c->evf) cudaEventDestroy(c->evf);
+  if (c->evj) cudaEventDestroy(c->evj);
+  for (auto& g : c->sweep_graph)
+    if (g) cudaGraphExecDestroy(g);
+  if (c->st2) cudaStreamDestroy(c->st2);
 }
 
 // ---------------------------------------------------------------------------
 // Building blocks
 // ---------------------------------------------------------------------------
 rnp_status run_stencil(rnp_ctx* c, bool fine, const double* in, double* out, double* out2,
-                       const Items& it) {
+                       const Items& it, cudaStream_t stream = nullptr) {
+  cudaStream_t sx = stream ? stream : c->st;
   const int scheme = fine ? SCHEME_RK4 : c->schemeG;
   const int steps = fine ? c->p.nF : c->p.nG;
   const double dt = fine ? c->dtF : c->dtG;
   cudaError_t e;
   if (c->plain)
     e = launch_stencil_plain(c->g, c->coef, scheme, steps, dt, in, out, out2, it,
-                             c->plain_work, c->st);
+                             c->plain_work, sx);
   else
     e = launch_stencil_fused(c->g, c->coef, c->fp32, scheme, steps, dt, in, out, out2, it,
-                             fine ? c->cfgF : c->cfgG, c->st);
+                             fine ? c->cfgF : c->cfgG, sx);
   if (e != cudaSuccess)
     return fail(c, RNP_ECUDA, "stencil launch failed: %s", cudaGetErrorString(e));
   return RNP_OK;
@@ -188,7 +201,7 @@ Items affine(int n, long long sb, long long ss, long long db, long long ds, cons
 
 rnp_status ensure_weights(rnp_ctx* c) {
   if (c->weights_ready) return RNP_OK;
-  CK(launch_weights(c->p.seed, c->M, c->d, c->A, c->zeta, nullptr, nullptr, nullptr, c->st));
+  CK(launch_weights(c->p.seed, c->M, c->d, c->A, c->zeta, c->A32, nullptr, nullptr, c->st));
   c->weights_ready = true;
   return RNP_OK;
 }
@@ -215,15 +228,109 @@ rnp_status predict_core(rnp_ctx* c, const double* q, long long q_base, long long
                         const int* gate) {
   Rows src{nullptr, q_base, q_bstride};
   Rows qrows{nullptr, 0, c->d};
-  CK(launch_scale_rows(c->g, q, src, nullptr, 1, c->sc, c->sr, c->qbuf, qrows, c->B, gate, c->st));
   Rows prow{nullptr, phi_base, phi_bstride};
-  CK(launch_features64(c->A, c->zeta, c->M, c->d, c->qbuf, qrows, c->B, phi_dst, prow,
-                       c->feat_part, gate, c->st));
-  const int pm = Pmax(c);
-  CK(launch_nn_partial(c->qbuf, c->Sds, c->cap, c->d, c->dP, pm, c->B, c->nn_part, gate, c->st));
+  // the neighbour grid is sized for up to 256 rows (rows are strided), so a
+  // captured sweep graph serves every later dataset size
+  const int pm = Pmax(c) > 0 ? (int)std::max<long long>(Pmax(c), std::min<long long>(c->cap, 256))
+                             : 0;
+  if (c->fp32) {
+    // mixed: FP32 query, FP32 features and FP32 distance screening
+    CK(launch_scale_rows(c->g, q, src, nullptr, 1, c->sc, c->sr, nullptr, c->q32, qrows, c->B,
+                         gate, c->st));
+    CK(launch_features32(c->A32, c->zeta, c->M, c->d, c->q32, qrows, c->B, phi_dst, prow,
+                         c->feat_part, gate, c->st));
+    CK(launch_nn_partial32(c->q32, c->S32, c->cap, c->d, c->dP, pm, c->B, c->nn_part, gate,
+                           c->st));
+  } else {
+    CK(launch_scale_rows(c->g, q, src, nullptr, 1, c->sc, c->sr, c->qbuf, nullptr, qrows, c->B,
+                         gate, c->st));
+    CK(launch_features64(c->A, c->zeta, c->M, c->d, c->qbuf, qrows, c->B, phi_dst, prow,
+                         c->feat_part, gate, c->st));
+    CK(launch_nn_partial(c->qbuf, c->Sds, c->cap, c->d, c->dP, pm, c->B, c->nn_part, gate,
+                         c->st));
+  }
   CK(launch_topm_ridge(c->nn_part, nn_chunks(c->d), c->Phi, c->cap, c->M, phi_dst + phi_base,
                        phi_bstride, c->dP, pm, c->B, c->m, c->p.lambda, c->dist, c->alpha,
                        c->idx, c->meff, c->flags + 0, c->flags + 1, gate, c->st));
+  return RNP_OK;
+}
+
+// One predictor-corrector step of Eq. 3 for every member, U[b][i] from
+// U[b][i-1] (U with member stride ubs).  G runs on the side stream while the
+// RandNet query (features, neighbours, ridge) runs on the main stream; both
+// read only U[b][i-1] and join before the update.  Gc (optional) receives
+// G(U[b][i-1]); err/gate as in launch_update.
+rnp_status sweep_step(rnp_ctx* c, double* U, long long ubs, int i, double* Gc,
+                      unsigned long long* err, const int* gate) {
+  const long long d = c->d, nb = (long long)c->N * d;
+  rnp_status s;
+  CK(cudaEventRecord(c->evf, c->st));
+  CK(cudaStreamWaitEvent(c->st2, c->evf, 0));
+  Items it = affine(c->B, (long long)(i - 1) * d, ubs, 0, d, gate);
+  if (Gc) {
+    it.dst2_base = (long long)(i - 1) * d;
+    it.dst2_stride = nb;
+  }
+  if ((s = run_stencil(c, false, U, c->gbuf, Gc, it, c->st2))) return s;
+  CK(cudaEventRecord(c->evj, c->st2));
+  if (c->randnet) {
+    if (Gc) {
+      // the solve caches the query's features as the next dataset row
+      if ((s = predict_core(c, U, (long long)(i - 1) * d, ubs, c->phic, (long long)(i - 1) * c->M,
+                            (long long)c->N * c->M, gate)))
+        return s;
+    } else if ((s = predict_core(c, U, (long long)(i - 1) * d, ubs, c->phiq, 0, c->M, gate))) {
+      return s;
+    }
+    CK(cudaStreamWaitEvent(c->st, c->evj, 0));
+    CK(launch_update(c->gbuf, d, c->Yds, c->cap, d, c->alpha, c->idx, c->meff,
+                     U + (long long)i * d, ubs, err ? err + i : nullptr, c->N + 1, c->flags + 2,
+                     c->B, gate, c->st));
+  } else {
+    CK(cudaStreamWaitEvent(c->st, c->evj, 0));
+    CK(launch_update_para(c->gbuf, d, c->Yv + (long long)(i - 1) * d, nb, d,
+                          U + (long long)i * d, ubs, err ? err + i : nullptr, c->N + 1,
+                          c->flags + 2, c->B, gate, c->st));
+  }
+  return RNP_OK;
+}
+
+// The solve's sweep i = i0 .. N.  In the fused path it is captured once per
+// i0 as a CUDA graph (every pointer is fixed per context; the gate table and
+// the dataset size are read from device memory) and replayed afterwards.
+rnp_status solve_sweep(rnp_ctx* c, int i0) {
+  const long long sb = (long long)(c->N + 1) * c->d;
+  rnp_status s;
+  if (c->plain) {
+    for (int i = i0; i <= c->N; ++i)
+      if ((s = sweep_step(c, c->U, sb, i, c->Gc, c->err, c->d_gate + (long long)i * c->B)))
+        return s;
+    return RNP_OK;
+  }
+  if (!c->sweep_graph[i0]) {
+    const long long before = launches_total();
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+    for (int i = i0; i <= c->N; ++i) {
+      s = sweep_step(c, c->U, sb, i, c->Gc, c->err, c->d_gate + (long long)i * c->B);
+      if (s) {
+        cudaStreamEndCapture(c->st, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+      }
+    }
+    CK(cudaStreamEndCapture(c->st, &graph));
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess)
+      return fail(c, RNP_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    c->sweep_graph[i0] = exec;
+    c->sweep_graph_launches[i0] = launches_total() - before;
+    count_launches(-c->sweep_graph_launches[i0]);  // captured, not launched
+  }
+  CK(cudaGraphLaunch(c->sweep_graph[i0], c->st));
+  count_launches(c->sweep_graph_launches[i0]);
   return RNP_OK;
 }
 
@@ -316,8 +423,13 @@ rnp_status rnp_create(const rnp_problem* prob, void* cuda_stream, rnp_ctx** out)
   ok &= dalloc(&c->qbuf, (size_t)B * d) == cudaSuccess;
   ok &= dalloc(&c->phic, (size_t)B * N * M) == cudaSuccess;
   ok &= dalloc(&c->phiq, (size_t)B * M) == cudaSuccess;
+  if (c->fp32) {
+    ok &= dalloc(&c->A32, (size_t)M * d) == cudaSuccess;
+    ok &= dalloc(&c->S32, (size_t)B * cap * d) == cudaSuccess;
+    ok &= dalloc(&c->q32, (size_t)B * d) == cudaSuccess;
+  }
   {
-    ok &= dalloc(&c->Sds, (size_t)B * cap * d) == cudaSuccess;
+    if (!c->fp32) ok &= dalloc(&c->Sds, (size_t)B * cap * d) == cudaSuccess;
     ok &= dalloc(&c->Yds, (size_t)B * cap * d) == cudaSuccess;
     ok &= dalloc(&c->Phi, (size_t)B * cap * M) == cudaSuccess;
     ok &= dalloc(&c->dist, (size_t)B * cap) == cudaSuccess;
@@ -345,6 +457,11 @@ rnp_status rnp_create(const rnp_problem* prob, void* cuda_stream, rnp_ctx** out)
   ok &= cudaMallocHost((void**)&c->h_err, sizeof(unsigned long long) * B * (N + 1)) == cudaSuccess;
   ok &= cudaMallocHost((void**)&c->h_flags, sizeof(int) * (4 + RNP_MAX_BATCH)) == cudaSuccess;
   for (auto& e : c->ev) ok &= cudaEventCreate(&e) == cudaSuccess;
+  ok &= cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking) == cudaSuccess;
+  ok &= cudaEventCreateWithFlags(&c->evf, cudaEventDisableTiming) == cudaSuccess;
+  ok &= cudaEventCreateWithFlags(&c->evj, cudaEventDisableTiming) == cudaSuccess;
+  c->sweep_graph.assign(N + 2, nullptr);
+  c->sweep_graph_launches.assign(N + 2, 0);
   if (!ok) {
     cudaGetLastError();
     char m[256];
@@ -481,12 +598,16 @@ rnp_status rnp_randnet_fit(rnp_ctx* c, const double* Uin, const double* Y, int P
     CK(cudaMemcpyAsync(c->d_app, c->h_app, sizeof(int) * c->itemcap, cudaMemcpyHostToDevice,
                        c->st));
     Rows rsrc{c->d_items, 0, 0}, rdst{c->d_items + c->itemcap, 0, 0};
-    CK(launch_scale_rows(c->g, Uin, rsrc, c->d_app, 1, c->sc, c->sr, c->Sds, rdst, n, nullptr,
-                         c->st));
+    CK(launch_scale_rows(c->g, Uin, rsrc, c->d_app, 1, c->sc, c->sr, c->fp32 ? nullptr : c->Sds,
+                         c->fp32 ? c->S32 : nullptr, rdst, n, nullptr, c->st));
     CK(launch_copy_rows(Y, c->d_items, c->Yds, c->d_items + c->itemcap, c->d, n, c->st));
     Rows prow{c->d_items + 2 * c->itemcap, 0, 0};
-    CK(launch_features64(c->A, c->zeta, c->M, c->d, c->Sds, rdst, n, c->Phi, prow,
-                         c->feat_part, nullptr, c->st));
+    if (c->fp32)
+      CK(launch_features32(c->A32, c->zeta, c->M, c->d, c->S32, rdst, n, c->Phi, prow,
+                           c->feat_part, nullptr, c->st));
+    else
+      CK(launch_features64(c->A, c->zeta, c->M, c->d, c->Sds, rdst, n, c->Phi, prow,
+                           c->feat_part, nullptr, c->st));
     CK(cudaStreamSynchronize(c->st));  // the staging tables are reused
   }
   for (int b = 0; b < c->B; ++b) c->P[b] += P;
@@ -533,11 +654,7 @@ rnp_status rnp_coarse_sweep(rnp_ctx* c, int first, const double* U_first, double
       if ((s = run_stencil(c, false, U, U, nullptr, it))) return s;
       continue;
     }
-    Items it = affine(c->B, (long long)(i - 1) * d, sb, 0, d, nullptr);
-    if ((s = run_stencil(c, false, U, c->gbuf, nullptr, it))) return s;
-    if ((s = predict_core(c, U, (long long)(i - 1) * d, sb, c->phiq, 0, c->M, nullptr))) return s;
-    CK(launch_update(c->gbuf, d, c->Yds, c->cap, d, c->alpha, c->idx, c->meff,
-                     U + (long long)i * d, sb, nullptr, 0, c->flags + 2, c->B, nullptr, c->st));
+    if ((s = sweep_step(c, U, sb, i, nullptr, nullptr, nullptr))) return s;
   }
   if (first == 0 && !use_fhat && c->p.scale_mode == RNP_SCALE_MINMAX) {
     CK(launch_scaling(c->g, U, sb, c->N + 1, c->B, false, c->sc, c->sr, c->scale_work,
@@ -639,14 +756,19 @@ rnp_status rnp_solve(rnp_ctx* c, const double* u0, double* Uout, rnp_stats* stat
 
     // ---- dataset append (Eq. 6) and features of the new rows -----------
     AppendItems ai{c->d_app, c->d_app + c->itemcap, c->d_app + 2 * c->itemcap, nit};
-    CK(launch_append(c->g, c->U, sb, c->Fv, c->Gc, nb, c->Yv, c->Sds, c->Yds, c->cap, c->sc,
+    CK(launch_append(c->g, c->U, sb, c->Fv, c->Gc, nb, c->Yv, c->fp32 ? nullptr : c->Sds,
+                     c->fp32 ? c->S32 : nullptr, c->Yds, c->cap, c->sc,
                      c->sr, ai, c->randnet, c->st));
     if (c->randnet) {
       if (k == 1) {
         Rows srows{c->d_items + 2 * c->itemcap, 0, 0};
         Rows prow{c->d_items + 3 * c->itemcap, 0, 0};
-        CK(launch_features64(c->A, c->zeta, M, d, c->Sds, srows, nit, c->Phi, prow,
-                             c->feat_part, nullptr, c->st));
+        if (c->fp32)
+          CK(launch_features32(c->A32, c->zeta, M, d, c->S32, srows, nit, c->Phi, prow,
+                               c->feat_part, nullptr, c->st));
+        else
+          CK(launch_features64(c->A, c->zeta, M, d, c->Sds, srows, nit, c->Phi, prow,
+                               c->feat_part, nullptr, c->st));
       } else {
         CK(launch_copy_phi(c->phic, (long long)N * M, c->Phi, c->cap, M, ai, c->st));
       }
@@ -667,25 +789,7 @@ rnp_status rnp_solve(rnp_ctx* c, const double* u0, double* Uout, rnp_stats* stat
     int imin = N + 1;
     for (int b = 0; b < B; ++b)
       if (!done[b]) imin = std::min(imin, L[b] + 2);
-    for (int i = imin; i <= N; ++i) {
-      const int* gate = c->d_gate + (long long)i * B;
-      Items it = affine(B, (long long)(i - 1) * d, sb, 0, d, gate);
-      it.dst2_base = (long long)(i - 1) * d;
-      it.dst2_stride = nb;
-      if ((s = run_stencil(c, false, c->U, c->gbuf, c->Gc, it))) return s;
-      if (c->randnet) {
-        if ((s = predict_core(c, c->U, (long long)(i - 1) * d, sb, c->phic,
-                              (long long)(i - 1) * M, (long long)N * M, gate)))
-          return s;
-        CK(launch_update(c->gbuf, d, c->Yds, c->cap, d, c->alpha, c->idx, c->meff,
-                         c->U + (long long)i * d, sb, c->err + i, N + 1, c->flags + 2, B, gate,
-                         c->st));
-      } else {
-        CK(launch_update_para(c->gbuf, d, c->Yv + (long long)(i - 1) * d, nb, d,
-                              c->U + (long long)i * d, sb, c->err + i, N + 1, c->flags + 2, B,
-                              gate, c->st));
-      }
-    }
+    if (imin <= N && (s = solve_sweep(c, imin))) return s;
     CK(cudaEventRecord(c->ev[3], c->st));
     CK(cudaMemcpyAsync(c->h_err, c->err, sizeof(unsigned long long) * B * (N + 1),
                        cudaMemcpyDeviceToHost, c->st));

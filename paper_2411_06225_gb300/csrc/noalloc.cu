@@ -26,7 +26,7 @@ static const int kNaMaxM = 1024;          // hidden neurons
 // | alpha [RNP_MAX_M] | scale c [3] | scale r [3]; then ints: P, meff,
 // idx [RNP_MAX_M], flags [4].
 static const long long kNaFeatCh = (kNaMaxD + 1023) / 1024;
-static const long long kNaNnCh = (kNaMaxD + 4095) / 4096;
+static const long long kNaNnCh = 32;  // nn_chunks(d) <= 32 for every d
 static const long long kNaDoubles = kNaMaxD + (long long)kNaMaxM * kNaFeatCh + kNaMaxM +
                                     (long long)kNaMaxP * kNaNnCh + kNaMaxP + RNP_MAX_M + 6;
 static const long long kNaInts = 2 + RNP_MAX_M + 4;
@@ -134,7 +134,8 @@ extern "C" rnp_status rnp_randnet_predict_noalloc(const rnp_problem* prob, const
   const long long d = g.d;
   const int M = prob->M;
   Rows qrow{nullptr, 0, d};
-  if ((e = launch_scale_rows(g, q, qrow, nullptr, 1, L.sc, L.sr, L.q, qrow, 1, nullptr, st)) ||
+  if ((e = launch_scale_rows(g, q, qrow, nullptr, 1, L.sc, L.sr, L.q, nullptr, qrow, 1, nullptr,
+                             st)) ||
       (e = launch_features64(A, zeta, M, d, L.q, qrow, 1, L.phiq, Rows{nullptr, 0, M},
                              L.feat_part, nullptr, st)) ||
       (e = launch_nn_partial(L.q, S, P, d, L.P, P, 1, L.nn_part, nullptr, st)) ||

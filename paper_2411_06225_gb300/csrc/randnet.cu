@@ -158,8 +158,8 @@ cudaError_t launch_scaling(const Geom& g, const double* U, long long bstride, in
 }
 
 __global__ void k_scale_rows(const double* U, Rows src, const int* row_b, int row_b_div,
-                             const double* c, const double* r, double* S, Rows dst, int R,
-                             long long n, long long d, const int* gate) {
+                             const double* c, const double* r, double* S, float* S32,
+                             Rows dst, int R, long long n, long long d, const int* gate) {
   const long long tot = (long long)R * d;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
        t += (long long)gridDim.x * blockDim.x) {
@@ -169,40 +169,45 @@ __global__ void k_scale_rows(const double* U, Rows src, const int* row_b, int ro
     const int q = (int)(e / n);
     const int b = row_b ? row_b[row] : row / row_b_div;
     const double u = U[item_off(src.off, src.base, src.stride, row) + e];
-    S[item_off(dst.off, dst.base, dst.stride, row) + e] =
-        __ddiv_rn(__dsub_rn(u, c[b * 3 + q]), r[b * 3 + q]);
+    const double v = __ddiv_rn(__dsub_rn(u, c[b * 3 + q]), r[b * 3 + q]);
+    const long long o = item_off(dst.off, dst.base, dst.stride, row) + e;
+    if (S) S[o] = v;
+    if (S32) S32[o] = (float)v;
   }
 }
 
 cudaError_t launch_scale_rows(const Geom& g, const double* U, Rows src, const int* row_b,
                               int row_b_div, const double* c, const double* r, double* S,
-                              Rows dst, int R, const int* gate, cudaStream_t st) {
+                              float* S32, Rows dst, int R, const int* gate, cudaStream_t st) {
   if (R <= 0) return cudaSuccess;
   count_launches(1);
   k_scale_rows<<<grid_cap((long long)R * g.d, 256), 256, 0, st>>>(
-      U, src, row_b, row_b_div, c, r, S, dst, R, g.n, g.d, gate);
+      U, src, row_b, row_b_div, c, r, S, S32, dst, R, g.n, g.d, gate);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// Random features, FP64 (Eq. HA).  Stage 1: for a chunk of CH coordinates
-// and a group of TR rows, every warp owns a set of neurons w and computes the
-// TR partial dot products A[w, chunk] . s[r, chunk] (lanes stride the chunk,
-// then a fixed butterfly reduction).  Stage 2 sums the chunk partials in
-// chunk order, adds zeta and applies ReLU.
+// Random features (Eq. HA), FP64 or FP32 operands.  Stage 1: a CTA takes a
+// chunk of CH coordinates, TR rows and FW neurons; every warp owns two
+// neurons and computes their TR partial dot products A[w, chunk] . s[r, chunk]
+// (lanes stride the chunk, then a fixed butterfly reduction).  Stage 2 sums
+// the chunk partials in chunk order (FP64), adds zeta and applies ReLU.
 // ---------------------------------------------------------------------------
 static const int kFeatCH = 1024;
 static const int kFeatTR = 4;
+static const int kFeatFW = 16;
 
 int features_chunks(long long d) { return (int)((d + kFeatCH - 1) / kFeatCH); }
 
-__global__ void __launch_bounds__(256) k_feat_partial(const double* A, int M, long long d,
-                                                      const double* S, Rows rows, int R,
+template <typename T>
+__global__ void __launch_bounds__(256) k_feat_partial(const T* A, int M, long long d,
+                                                      const T* S, Rows rows, int R,
                                                       double* part, int nch,
                                                       const int* gate) {
-  __shared__ double sS[kFeatTR][kFeatCH];
+  __shared__ T sS[kFeatTR][kFeatCH];
   const int ch = blockIdx.x;
   const int r0 = blockIdx.y * kFeatTR;
+  const int w0 = blockIdx.z * kFeatFW;
   const long long j0 = (long long)ch * kFeatCH;
   const int len = (int)((d - j0) < kFeatCH ? (d - j0) : kFeatCH);
   bool any = false;
@@ -210,27 +215,27 @@ __global__ void __launch_bounds__(256) k_feat_partial(const double* A, int M, lo
     const int row = r0 + r;
     const bool on = row < R && (!gate || gate[row]);
     any |= on;
-    const double* src = on ? S + item_off(rows.off, rows.base, rows.stride, row) + j0 : nullptr;
+    const T* src = on ? S + item_off(rows.off, rows.base, rows.stride, row) + j0 : nullptr;
     for (int j = threadIdx.x; j < kFeatCH; j += blockDim.x)
-      sS[r][j] = (on && j < len) ? src[j] : 0.0;
+      sS[r][j] = (on && j < len) ? src[j] : T(0);
   }
   if (!any) return;
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nw = blockDim.x >> 5;
-  for (int w = warp; w < M; w += nw) {
-    const double* Aw = A + (long long)w * d + j0;
-    double acc[kFeatTR];
+  for (int w = w0 + warp; w < M && w < w0 + kFeatFW; w += 8) {
+    const T* Aw = A + (long long)w * d + j0;
+    T acc[kFeatTR];
 #pragma unroll
-    for (int r = 0; r < kFeatTR; ++r) acc[r] = 0.0;
+    for (int r = 0; r < kFeatTR; ++r) acc[r] = T(0);
+#pragma unroll 4
     for (int j = lane; j < len; j += 32) {
-      const double a = Aw[j];
+      const T a = Aw[j];
 #pragma unroll
       for (int r = 0; r < kFeatTR; ++r) acc[r] = fma(a, sS[r][j], acc[r]);
     }
 #pragma unroll
     for (int r = 0; r < kFeatTR; ++r) {
-      double v = acc[r];
+      T v = acc[r];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
       acc[r] = v;
@@ -238,7 +243,7 @@ __global__ void __launch_bounds__(256) k_feat_partial(const double* A, int M, lo
     if (lane == 0) {
 #pragma unroll
       for (int r = 0; r < kFeatTR; ++r)
-        if (r0 + r < R) part[((long long)(r0 + r) * M + w) * nch + ch] = acc[r];
+        if (r0 + r < R) part[((long long)(r0 + r) * M + w) * nch + ch] = (double)acc[r];
     }
   }
 }
@@ -256,63 +261,111 @@ __global__ void k_feat_finish(const double* part, int nch, int R, int M, const d
   phi[item_off(prow.off, prow.base, prow.stride, row) + w] = v > 0.0 ? v : 0.0;
 }
 
-cudaError_t launch_features64(const double* A, const double* zeta, int M, long long d,
-                              const double* S, Rows s_rows, int R, double* phi,
-                              Rows phi_rows, double* part, const int* gate,
-                              cudaStream_t st) {
+template <typename T>
+static cudaError_t launch_features_t(const T* A, const double* zeta, int M, long long d,
+                                     const T* S, Rows s_rows, int R, double* phi,
+                                     Rows phi_rows, double* part, const int* gate,
+                                     cudaStream_t st) {
   if (R <= 0) return cudaSuccess;
   const int nch = features_chunks(d);
-  dim3 grid(nch, (R + kFeatTR - 1) / kFeatTR);
-  count_launches(1);
-  k_feat_partial<<<grid, 256, 0, st>>>(A, M, d, S, s_rows, R, part, nch, gate);
-  count_launches(1);
+  dim3 grid(nch, (R + kFeatTR - 1) / kFeatTR, (M + kFeatFW - 1) / kFeatFW);
+  count_launches(2);
+  k_feat_partial<T><<<grid, 256, 0, st>>>(A, M, d, S, s_rows, R, part, nch, gate);
   k_feat_finish<<<(R * M + 255) / 256, 256, 0, st>>>(part, nch, R, M, zeta, phi, phi_rows,
                                                      gate);
   return cudaGetLastError();
 }
 
+cudaError_t launch_features64(const double* A, const double* zeta, int M, long long d,
+                              const double* S, Rows s_rows, int R, double* phi,
+                              Rows phi_rows, double* part, const int* gate,
+                              cudaStream_t st) {
+  return launch_features_t<double>(A, zeta, M, d, S, s_rows, R, phi, phi_rows, part, gate, st);
+}
+
+cudaError_t launch_features32(const float* A, const double* zeta, int M, long long d,
+                              const float* S, Rows s_rows, int R, double* phi,
+                              Rows phi_rows, double* part, const int* gate,
+                              cudaStream_t st) {
+  return launch_features_t<float>(A, zeta, M, d, S, s_rows, R, phi, phi_rows, part, gate, st);
+}
+
 // ---------------------------------------------------------------------------
 // Nearest-neighbour distances (App. B): delta_p = sum_j (q_j - S_pj)^2.
-// One warp per stored row and chunk; chunk partials are summed in order by
-// the selection kernel.
+// One warp per stored row and chunk (at most 32 chunks per state); chunk
+// partials are summed in chunk order by the selection kernel.
 // ---------------------------------------------------------------------------
-static const int kNnCH = 4096;
 static const int kNnRows = 8;
 
-int nn_chunks(long long d) { return (int)((d + kNnCH - 1) / kNnCH); }
+static long long nn_chunk_len(long long d) {
+  long long ch = (d + 31) / 32;
+  ch = ((ch + 255) / 256) * 256;
+  return ch < 1024 ? 1024 : ch;
+}
 
-__global__ void __launch_bounds__(256) k_nn_partial(const double* q, const double* S,
-                                                    long long cap, long long d, const int* P,
-                                                    double* part, int nch, const int* gate) {
+int nn_chunks(long long d) { return (int)((d + nn_chunk_len(d) - 1) / nn_chunk_len(d)); }
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_nn_partial(const T* q, const T* S, long long cap,
+                                                    long long d, long long chl,
+                                                    const int* P, double* part, int nch,
+                                                    const int* gate) {
   const int b = blockIdx.z;
   if (gate && !gate[b]) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int p = blockIdx.y * kNnRows + warp;
-  if (p >= P[b]) return;
+  const int Pb = P[b];
   const int ch = blockIdx.x;
-  const long long j0 = (long long)ch * kNnCH;
-  const long long j1 = (j0 + kNnCH) < d ? j0 + kNnCH : d;
-  const double* qb = q + (long long)b * d;
-  const double* Sp = S + ((long long)b * cap + p) * d;
-  double acc = 0.0;
-  for (long long j = j0 + lane; j < j1; j += 32) {
-    const double t = qb[j] - Sp[j];
-    acc = fma(t, t, acc);
-  }
+  const long long j0 = (long long)ch * chl;
+  const long long j1 = (j0 + chl) < d ? j0 + chl : d;
+  const T* qb = q + (long long)b * d;
+  // grid-stride over the stored rows: the grid does not depend on P
+  for (int p = blockIdx.y * kNnRows + warp; p < Pb; p += gridDim.y * kNnRows) {
+    const T* Sp = S + ((long long)b * cap + p) * d;
+    T acc0 = T(0), acc1 = T(0);
+    long long j = j0 + lane;
+    for (; j + 32 < j1; j += 64) {
+      const T t0 = qb[j] - Sp[j];
+      const T t1 = qb[j + 32] - Sp[j + 32];
+      acc0 = fma(t0, t0, acc0);
+      acc1 = fma(t1, t1, acc1);
+    }
+    if (j < j1) {
+      const T t0 = qb[j] - Sp[j];
+      acc0 = fma(t0, t0, acc0);
+    }
+    T acc = acc0 + acc1;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) part[((long long)b * cap + p) * nch + ch] = acc;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) part[((long long)b * cap + p) * nch + ch] = (double)acc;
+  }
+}
+
+template <typename T>
+static cudaError_t launch_nn_t(const T* q, const T* S, long long cap, long long d, const int* P,
+                               int Pmax, int B, double* part, const int* gate,
+                               cudaStream_t st) {
+  if (Pmax <= 0 || B <= 0) return cudaSuccess;
+  const int nch = nn_chunks(d);
+  // Pmax only sizes the grid (rows are strided), so a graph captured with
+  // the arena capacity stays valid as the dataset grows
+  int gy = (Pmax + kNnRows - 1) / kNnRows;
+  if (gy > 32) gy = 32;
+  dim3 grid(nch, gy, B);
+  count_launches(1);
+  k_nn_partial<T><<<grid, 256, 0, st>>>(q, S, cap, d, nn_chunk_len(d), P, part, nch, gate);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_nn_partial(const double* q, const double* S, long long cap, long long d,
                               const int* P, int Pmax, int B, double* part, const int* gate,
                               cudaStream_t st) {
-  if (Pmax <= 0 || B <= 0) return cudaSuccess;
-  const int nch = nn_chunks(d);
-  dim3 grid(nch, (Pmax + kNnRows - 1) / kNnRows, B);
-  count_launches(1);
-  k_nn_partial<<<grid, 256, 0, st>>>(q, S, cap, d, P, part, nch, gate);
-  return cudaGetLastError();
+  return launch_nn_t<double>(q, S, cap, d, P, Pmax, B, part, gate, st);
+}
+
+cudaError_t launch_nn_partial32(const float* q, const float* S, long long cap, long long d,
+                                const int* P, int Pmax, int B, double* part, const int* gate,
+                                cudaStream_t st) {
+  return launch_nn_t<float>(q, S, cap, d, P, Pmax, B, part, gate, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -376,27 +429,32 @@ __global__ void __launch_bounds__(256) k_topm_ridge(const double* part, int nch,
     }
     __syncthreads();
   }
-  // Gram entries K[i][j] = sum_w X_i,w X_j,w (i >= j) and rhs_i = X_i . phi_q,
-  // summed over w in ascending order.
+  // Gram entries K[i][j] = sum_w X_i,w X_j,w (i >= j) and rhs_i = X_i . phi_q:
+  // one warp per entry, lanes stride w, fixed butterfly reduction.
   const double* X = Phi + (long long)b * cap * M;
   const double* pq = phiq + (long long)b * phiq_bstride;
   const int nK = me * (me + 1) / 2;
-  for (int t = threadIdx.x; t < nK + me; t += blockDim.x) {
+  for (int t = warp; t < nK + me; t += nw) {
+    const double *xa, *xb;
+    int i, j = -1;
     if (t < nK) {
-      int i = 0;
+      i = 0;
       while ((i + 1) * (i + 2) / 2 <= t) ++i;
-      const int j = t - i * (i + 1) / 2;
-      const double* xi = X + (long long)sel[i] * M;
-      const double* xj = X + (long long)sel[j] * M;
-      double acc = 0.0;
-      for (int w = 0; w < M; ++w) acc = __dadd_rn(acc, __dmul_rn(xi[w], xj[w]));
-      Kraw[i * RNP_MAX_M + j] = acc;
+      j = t - i * (i + 1) / 2;
+      xa = X + (long long)sel[i] * M;
+      xb = X + (long long)sel[j] * M;
     } else {
-      const int i = t - nK;
-      const double* xi = X + (long long)sel[i] * M;
-      double acc = 0.0;
-      for (int w = 0; w < M; ++w) acc = __dadd_rn(acc, __dmul_rn(xi[w], pq[w]));
-      rhs[i] = acc;
+      i = t - nK;
+      xa = X + (long long)sel[i] * M;
+      xb = pq;
+    }
+    double acc = 0.0;
+    for (int w = lane; w < M; w += 32) acc = fma(xa[w], xb[w], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      if (j >= 0) Kraw[i * RNP_MAX_M + j] = acc;
+      else rhs[i] = acc;
     }
   }
   __syncthreads();
@@ -538,8 +596,8 @@ __global__ void __launch_bounds__(256) k_update_para(const double* g, long long 
 }
 
 static dim3 update_grid(long long d, int B) {
-  long long bx = (d + 256 * 4 - 1) / (256 * 4);
-  if (bx > 152) bx = 152;
+  long long bx = (d + 255) / 256;
+  if (bx > 1024) bx = 1024;
   if (bx < 1) bx = 1;
   return dim3((unsigned)bx, B);
 }
@@ -572,8 +630,9 @@ cudaError_t launch_update_para(const double* g, long long g_bstride, const doubl
 // ---------------------------------------------------------------------------
 __global__ void k_append(const double* U, long long u_bstride, const double* Fv,
                          const double* Gc, long long n_bstride, double* Yv, double* Sds,
-                         double* Yds, long long cap, const double* c, const double* r,
-                         AppendItems it, bool randnet, long long n, long long d) {
+                         float* S32, double* Yds, long long cap, const double* c,
+                         const double* r, AppendItems it, bool randnet, long long n,
+                         long long d) {
   const long long tot = (long long)it.n * d;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
        t += (long long)gridDim.x * blockDim.x) {
@@ -588,19 +647,22 @@ __global__ void k_append(const double* U, long long u_bstride, const double* Fv,
       Yds[ds] = y;
       const int q = (int)(e / n);
       const double u = U[(long long)b * u_bstride + (long long)j * d + e];
-      Sds[ds] = __ddiv_rn(__dsub_rn(u, c[b * 3 + q]), r[b * 3 + q]);
+      const double v = __ddiv_rn(__dsub_rn(u, c[b * 3 + q]), r[b * 3 + q]);
+      if (Sds) Sds[ds] = v;
+      if (S32) S32[ds] = (float)v;
     }
   }
 }
 
 cudaError_t launch_append(const Geom& g, const double* U, long long u_bstride, const double* Fv,
                           const double* Gc, long long n_bstride, double* Yv, double* Sds,
-                          double* Yds, long long cap, const double* c, const double* r,
-                          const AppendItems& it, bool randnet, cudaStream_t st) {
+                          float* S32, double* Yds, long long cap, const double* c,
+                          const double* r, const AppendItems& it, bool randnet,
+                          cudaStream_t st) {
   if (it.n <= 0) return cudaSuccess;
   count_launches(1);
   k_append<<<grid_cap((long long)it.n * g.d, 256), 256, 0, st>>>(
-      U, u_bstride, Fv, Gc, n_bstride, Yv, Sds, Yds, cap, c, r, it, randnet, g.n, g.d);
+      U, u_bstride, Fv, Gc, n_bstride, Yv, Sds, S32, Yds, cap, c, r, it, randnet, g.n, g.d);
   return cudaGetLastError();
 }
 

@@ -113,17 +113,23 @@ cudaError_t launch_scaling(const Geom& g, const double* U, long long bstride,
                            int nstates, int B, bool none, double* c, double* r,
                            double* work, int* nonfinite, cudaStream_t st);
 
-// Rows r = 0..R-1: S[dst_off[r]..] = (U[src_off[r]..] - c[b]) / r[b]
-// with b = row_b[r].
+// Rows r = 0..R-1: S[dst(r)..] = (U[src(r)..] - c[b]) / r[b] with
+// b = row_b[r] (or r / row_b_div); S (FP64) and S32 (rounded to FP32) are
+// each optional.
 cudaError_t launch_scale_rows(const Geom& g, const double* U, Rows src,
                               const int* row_b, int row_b_div,
                               const double* c, const double* r, double* S,
-                              Rows dst, int R, const int* gate, cudaStream_t st);
+                              float* S32, Rows dst, int R, const int* gate,
+                              cudaStream_t st);
 
 // Random features phi = ReLU(A s + zeta) of R scaled rows S + s_off[r],
 // written to phi + phi_off[r] (FP64).  part must hold R * M * nchunks.
 cudaError_t launch_features64(const double* A, const double* zeta, int M,
                               long long d, const double* S, Rows s_rows, int R,
+                              double* phi, Rows phi_rows, double* part,
+                              const int* gate, cudaStream_t st);
+cudaError_t launch_features32(const float* A, const double* zeta, int M,
+                              long long d, const float* S, Rows s_rows, int R,
                               double* phi, Rows phi_rows, double* part,
                               const int* gate, cudaStream_t st);
 int features_chunks(long long d);
@@ -133,6 +139,9 @@ int features_chunks(long long d);
 cudaError_t launch_nn_partial(const double* q, const double* S, long long cap,
                               long long d, const int* P, int Pmax, int B,
                               double* part, const int* gate, cudaStream_t st);
+cudaError_t launch_nn_partial32(const float* q, const float* S, long long cap,
+                                long long d, const int* P, int Pmax, int B,
+                                double* part, const int* gate, cudaStream_t st);
 int nn_chunks(long long d);
 
 // Per member: finish distances, select the m nearest (ties -> lower index),
@@ -176,8 +185,8 @@ struct AppendItems {
 };
 cudaError_t launch_append(const Geom& g, const double* U, long long u_bstride,
                           const double* Fv, const double* Gc, long long n_bstride,
-                          double* Yv, double* Sds, double* Yds, long long cap,
-                          const double* c, const double* r,
+                          double* Yv, double* Sds, float* S32, double* Yds,
+                          long long cap, const double* c, const double* r,
                           const AppendItems& it, bool randnet, cudaStream_t st);
 
 // Copy feature rows: dst[b][p] = src[b][j] for each append item.
