@@ -25,7 +25,9 @@ struct rnp_ctx {
   Geom g;
   Coef coef;
   int dev = 0;
-  cudaStream_t st = nullptr;
+  cudaStream_t ust = nullptr;  // the caller's stream
+  cudaStream_t st = nullptr;   // the context's own stream (capturable)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   int B = 1, N = 1, M = 1, m = 1;
   long long d = 0, cap = 0;
   bool fp32 = false, plain = false, randnet = true;
@@ -86,6 +88,22 @@ struct DevGuard {
   ~DevGuard() {
     int cur;
     if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// Orders a call's work after what the caller enqueued on its stream, and
+// the caller's later work after the call's: the context computes on its own
+// stream (which, unlike the legacy default stream, can be captured into a
+// graph) joined to the caller's stream by events.
+struct StreamJoin {
+  rnp_ctx* c;
+  explicit StreamJoin(rnp_ctx* ctx) : c(ctx) {
+    cudaEventRecord(c->ev_in, c->ust);
+    cudaStreamWaitEvent(c->st, c->ev_in, 0);
+  }
+  ~StreamJoin() {
+    cudaEventRecord(c->ev_out, c->st);
+    cudaStreamWaitEvent(c->ust, c->ev_out, 0);
   }
 };
 
@@ -166,6 +184,9 @@ void destroy_buffers(rnp_ctx* c) {
   for (auto& g : c->sweep_graph)
     if (g) cudaGraphExecDestroy(g);
   if (c->st2) cudaStreamDestroy(c->st2);
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
+  if (c->st) cudaStreamDestroy(c->st);
 }
 
 // ---------------------------------------------------------------------------
@@ -375,7 +396,7 @@ rnp_status rnp_create(const rnp_problem* prob, void* cuda_stream, rnp_ctx** out)
     delete c;
     return fail(nullptr, RNP_ECUDA, "no CUDA device");
   }
-  c->st = (cudaStream_t)cuda_stream;
+  c->ust = (cudaStream_t)cuda_stream;
   c->g = make_geom(*prob);
   c->coef = make_coef(*prob, c->g);
   c->B = prob->batch; c->N = prob->N; c->M = prob->M; c->m = prob->m;
@@ -457,6 +478,9 @@ rnp_status rnp_create(const rnp_problem* prob, void* cuda_stream, rnp_ctx** out)
   ok &= cudaMallocHost((void**)&c->h_err, sizeof(unsigned long long) * B * (N + 1)) == cudaSuccess;
   ok &= cudaMallocHost((void**)&c->h_flags, sizeof(int) * (4 + RNP_MAX_BATCH)) == cudaSuccess;
   for (auto& e : c->ev) ok &= cudaEventCreate(&e) == cudaSuccess;
+  ok &= cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) == cudaSuccess;
+  ok &= cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) == cudaSuccess;
+  ok &= cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) == cudaSuccess;
   ok &= cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking) == cudaSuccess;
   ok &= cudaEventCreateWithFlags(&c->evf, cudaEventDisableTiming) == cudaSuccess;
   ok &= cudaEventCreateWithFlags(&c->evj, cudaEventDisableTiming) == cudaSuccess;
@@ -485,7 +509,8 @@ rnp_status rnp_create(const rnp_problem* prob, void* cuda_stream, rnp_ctx** out)
 rnp_status rnp_destroy(rnp_ctx* c) {
   if (!c) return RNP_OK;
   DevGuard gd(c->dev);
-  cudaStreamSynchronize(c->st);
+  if (c->st) cudaStreamSynchronize(c->st);
+  if (c->st2) cudaStreamSynchronize(c->st2);
   destroy_buffers(c);
   delete c;
   return RNP_OK;
@@ -496,6 +521,7 @@ rnp_status rnp_fine_batch(rnp_ctx* c, const double* U_in, int n, double* U_out) 
   c->msg.clear();
   if (!U_in || !U_out || n < 1 || n > c->N) return fail(c, RNP_EINVAL, "bad arguments");
   DevGuard gd(c->dev);
+  StreamJoin sj(c);
   Items it = affine(c->B * n, 0, c->d, 0, c->d, nullptr);
   if (!c->plain && c->B * n > c->B * c->N) return fail(c, RNP_EINVAL, "too many items");
   return run_stencil(c, true, U_in, U_out, nullptr, it);
@@ -505,6 +531,7 @@ rnp_status rnp_get_weights(rnp_ctx* c, double* A, double* zeta) {
   if (!c) return RNP_EINVAL;
   c->msg.clear();
   DevGuard gd(c->dev);
+  StreamJoin sj(c);
   rnp_status s = ensure_weights(c);
   if (s) return s;
   if (A) CK(cudaMemcpyAsync(A, c->A, sizeof(double) * c->M * c->d, cudaMemcpyDeviceToDevice, c->st));
@@ -517,6 +544,7 @@ rnp_status rnp_set_scaling(rnp_ctx* c, const double* hc, const double* hr) {
   c->msg.clear();
   if (!hc || !hr) return fail(c, RNP_EINVAL, "NULL scaling");
   DevGuard gd(c->dev);
+  StreamJoin sj(c);
   for (int i = 0; i < c->B * 3; ++i) {
     if (!(hr[i] != 0.0)) return fail(c, RNP_EINVAL, "scale r must be nonzero");
     c->h_c[i] = hc[i];
@@ -533,6 +561,7 @@ rnp_status rnp_get_scaling(rnp_ctx* c, double* hc, double* hr) {
   if (!c) return RNP_EINVAL;
   c->msg.clear();
   DevGuard gd(c->dev);
+  StreamJoin sj(c);
   if (!c->scaling_ready) {
     for (int i = 0; i < c->B * 3; ++i) { hc[i] = 0.0; hr[i] = 1.0; }
     return RNP_OK;
@@ -547,6 +576,7 @@ rnp_status rnp_reset(rnp_ctx* c) {
   if (!c) return RNP_EINVAL;
   c->msg.clear();
   DevGuard gd(c->dev);
+  StreamJoin sj(c);
   std::fill(c->P.begin(), c->P.end(), 0);
   c->scaling_ready = false;
   return upload_P(c);
@@ -571,6 +601,7 @@ rnp_status rnp_randnet_fit(rnp_ctx* c, const double* Uin, const double* Y, int P
   if (!Uin || !Y || P < 0) return fail(c, RNP_EINVAL, "bad arguments");
   if (P == 0) return RNP_OK;
   DevGuard gd(c->dev);
+  StreamJoin sj(c);
   for (int b = 0; b < c->B; ++b)
     if (c->P[b] + (long long)P > c->cap)
       return fail(c, RNP_ENOMEM, "dataset arena full (%lld rows per member)", c->cap);
@@ -619,6 +650,7 @@ rnp_status rnp_randnet_predict(rnp_ctx* c, const double* q, double* out) {
   c->msg.clear();
   if (!q || !out) return fail(c, RNP_EINVAL, "bad arguments");
   DevGuard gd(c->dev);
+  StreamJoin sj(c);
   rnp_status s = ensure_weights(c);
   if (s) return s;
   if ((s = ensure_scaling_identity(c))) return s;
@@ -637,6 +669,7 @@ rnp_status rnp_coarse_sweep(rnp_ctx* c, int first, const double* U_first, double
   c->msg.clear();
   if (!U_first || !U || first < 0 || first > c->N) return fail(c, RNP_EINVAL, "bad arguments");
   DevGuard gd(c->dev);
+  StreamJoin sj(c);
   const long long d = c->d, sb = (long long)(c->N + 1) * d;
   CK(cudaMemcpy2DAsync(U + (long long)first * d, sizeof(double) * sb, U_first,
                        sizeof(double) * d, sizeof(double) * d, c->B, cudaMemcpyDeviceToDevice,
@@ -673,6 +706,7 @@ rnp_status rnp_solve(rnp_ctx* c, const double* u0, double* Uout, rnp_stats* stat
   c->msg.clear();
   if (!u0 || !Uout) return fail(c, RNP_EINVAL, "bad arguments");
   DevGuard gd(c->dev);
+  StreamJoin sj(c);
   auto t_start = std::chrono::steady_clock::now();
   const long long launches0 = launches_total();
   const int B = c->B, N = c->N, M = c->M;
