@@ -186,8 +186,9 @@ def run_gpu(args):
     u0_h = torch.as_tensor(W.initial_condition(cfg)).pin_memory()
     u0 = u0_h.to(dev)
     stream = torch.cuda.current_stream(dev)
-    prob = rnp.problem(cfg, precision=args.precision, exec="fused")
+    prob = rnp.problem(cfg, precision=args.precision, exec="fused", autotune=1)
     solver = rnp.Solver(prob, stream=stream)
+    tiling = {"fine": solver.stencil_config("fine"), "coarse": solver.stencil_config("coarse")}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
 
     for _ in range(args.warmup):
@@ -281,12 +282,13 @@ def run_gpu(args):
             "data": "synthetic",
             "config": {"workload": f"{WORKLOAD} 128x128x2 periodic, N=64, F=RK4x2000, "
                                    "G=Eulerx8, M=100, m=4, tol=1e-6",
-                       "precision": args.precision, "exec": "fused",
+                       "precision": args.precision, "exec": "fused", "autotune": True,
                        "replica_per_rank": True, "l2": "flushed between timed steps "
                        "(256 MB write)", "parallelism": f"replicas x{ws}"},
             "time_to_solution_ms": {"p50": statistics.median(tts), "min": min(tts),
                                     "max": max(tts)},
             "K": stats["K"], "fine_ms_per_iteration": statistics.mean(fine_ms),
+            "stencil_tiling": tiling,
             "sweep_ms": stats["t_sweep_ms"], "fit_ms": stats["t_fit_ms"],
             "roofline": {"kernel": "k_stencil_fused<DIFFREACT,float>", "bound": "alu",
                          "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",

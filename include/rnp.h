@@ -117,6 +117,9 @@ typedef struct {
   int threads;            /* fused stencil: threads per CTA (0 = auto)      */
   long long max_pairs;    /* dataset rows per member (0 = enough for
                              max_iters iterations)                          */
+  int autotune;           /* 1: rnp_create times every launchable stencil
+                             tiling on the context's buffers and keeps the
+                             fastest (ignored when cluster/threads are set) */
 } rnp_problem;
 
 typedef struct {
@@ -203,6 +206,11 @@ rnp_status rnp_reset(rnp_ctx* ctx);
 rnp_status rnp_get_pairs(rnp_ctx* ctx, long long* pairs);
 /* Unknowns per state. */
 long long rnp_dim(const rnp_problem* prob);
+/* Stencil launch configuration in use: which = 0 fine step, 1 coarse step.
+ * out[0] cluster size, out[1] threads per CTA, out[2] x-points per thread
+ * (0 for the FP64 kernel), out[3] rows per thread, out[4] 1 if chosen by
+ * timing.  Host out. */
+rnp_status rnp_stencil_config(const rnp_ctx* ctx, int which, int* out);
 
 /* --- allocation-free prediction (no counterpart in the paper) ----------- */
 

@@ -48,7 +48,7 @@ class Problem(C.Structure):
         ("tol", C.c_double), ("max_iters", C.c_int), ("corr", C.c_int),
         ("scale_mode", C.c_int), ("gscheme", C.c_int), ("precision", C.c_int),
         ("exec_", C.c_int), ("batch", C.c_int), ("cluster", C.c_int),
-        ("threads", C.c_int), ("max_pairs", C.c_longlong),
+        ("threads", C.c_int), ("max_pairs", C.c_longlong), ("autotune", C.c_int),
     ]
 
 
@@ -94,6 +94,7 @@ def problem(cfg: dict, precision: str = "fp64", exec: str = "fused", **kw) -> Pr
     p.cluster = c.get("cluster", 0)
     p.threads = c.get("threads", 0)
     p.max_pairs = c.get("max_pairs", 0)
+    p.autotune = int(c.get("autotune", 0))
     return p
 
 
@@ -138,6 +139,7 @@ def lib() -> C.CDLL:
         "rnp_reset": (C.c_int, [vp]),
         "rnp_get_pairs": (C.c_int, [vp, C.POINTER(C.c_longlong)]),
         "rnp_dim": (C.c_longlong, [C.POINTER(Problem)]),
+        "rnp_stencil_config": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int)]),
         "rnp_randnet_predict_noalloc": (C.c_int, [
             C.POINTER(Problem), dp, dp, dp, dp, dp, C.c_int, C.POINTER(C.c_double),
             C.POINTER(C.c_double), dp, dp, dp, vp]),
@@ -275,6 +277,11 @@ class Solver:
 
     def reset(self):
         self._check(lib().rnp_reset(self._ctx))
+
+    def stencil_config(self, which: str = "fine") -> dict:
+        out = (C.c_int * 5)()
+        self._check(lib().rnp_stencil_config(self._ctx, {"fine": 0, "coarse": 1}[which], out))
+        return dict(cluster=out[0], threads=out[1], px=out[2], rs=out[3], tuned=bool(out[4]))
 
     def pairs(self):
         out = (C.c_longlong * self.B)()

@@ -32,6 +32,7 @@ struct rnp_ctx {
   long long d = 0, cap = 0;
   bool fp32 = false, plain = false, randnet = true;
   StencilCfg cfgF{}, cfgG{};
+  bool tunedF = false, tunedG = false;
   double dtF = 0, dtG = 0;
   int schemeG = SCHEME_EULER;
 
@@ -364,6 +365,48 @@ rnp_status read_flags(rnp_ctx* c, int* esc, int* failf, int* nonfinite) {
   return RNP_OK;
 }
 
+// Times every launchable stencil tiling for the fine step (all B N slices)
+// and the coarse step (one item per member) on the context's own buffers,
+// a few steps each after one untimed launch, and keeps the fastest.  The
+// cost of a step does not depend on the state's values.
+rnp_status autotune_stencils(rnp_ctx* c) {
+  const int B = c->B, N = c->N;
+  const long long d = c->d, sb = (long long)(N + 1) * d;
+  CK(cudaMemsetAsync(c->U, 0, sizeof(double) * B * sb, c->st));
+  CK(cudaMemsetAsync(c->Fv, 0, sizeof(double) * B * N * d, c->st));
+  for (int which = 0; which < 2; ++which) {
+    const bool fine = which == 0;
+    const int nitems = fine ? B * N : B;
+    StencilCfg cands[64];
+    const int n = list_stencil_cfgs(c->g, c->fp32, nitems, cands, 64);
+    if (n <= 1) continue;
+    const int steps = std::min(fine ? c->p.nF : c->p.nG, fine ? 16 : 8);
+    Items it = affine(nitems, 0, d, 0, d, nullptr);
+    float best = 1e30f;
+    int besti = -1;
+    for (int k = 0; k < n; ++k) {
+      float tmin = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {
+        CK(cudaEventRecord(c->ev[4], c->st));
+        CK(launch_stencil_fused(c->g, c->coef, c->fp32, fine ? SCHEME_RK4 : c->schemeG, steps,
+                                fine ? c->dtF : c->dtG, c->U, c->Fv, nullptr, it, cands[k],
+                                c->st));
+        CK(cudaEventRecord(c->ev[5], c->st));
+        CK(cudaEventSynchronize(c->ev[5]));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, c->ev[4], c->ev[5]));
+        if (rep > 0 && ms < tmin) tmin = ms;
+      }
+      if (tmin < best) { best = tmin; besti = k; }
+    }
+    if (besti >= 0) {
+      if (fine) { c->cfgF = cands[besti]; c->tunedF = true; }
+      else { c->cfgG = cands[besti]; c->tunedG = true; }
+    }
+  }
+  return RNP_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -502,6 +545,12 @@ rnp_status rnp_create(const rnp_problem* prob, void* cuda_stream, rnp_ctx** out)
     return bail(RNP_ECUDA, "initialisation failed");
   }
   for (int i = 0; i < B * 3; ++i) { c->h_c[i] = 0.0; c->h_r[i] = 1.0; }
+  if (prob->autotune && !c->plain && prob->cluster == 0 && prob->threads == 0) {
+    if (autotune_stencils(c) != RNP_OK) {
+      std::string m = "autotune: " + c->msg;
+      return bail(RNP_ECUDA, m.c_str());
+    }
+  }
   *out = c;
   return RNP_OK;
 }
@@ -580,6 +629,17 @@ rnp_status rnp_reset(rnp_ctx* c) {
   std::fill(c->P.begin(), c->P.end(), 0);
   c->scaling_ready = false;
   return upload_P(c);
+}
+
+rnp_status rnp_stencil_config(const rnp_ctx* c, int which, int* out) {
+  if (!c || !out || (which != 0 && which != 1)) return RNP_EINVAL;
+  const StencilCfg& s = which == 0 ? c->cfgF : c->cfgG;
+  out[0] = c->plain ? 0 : s.cluster;
+  out[1] = c->plain ? 256 : s.threads;
+  out[2] = s.px;
+  out[3] = s.px ? s.rs : s.R;
+  out[4] = which == 0 ? c->tunedF : c->tunedG;
+  return RNP_OK;
 }
 
 rnp_status rnp_get_pairs(rnp_ctx* c, long long* pairs) {

@@ -84,6 +84,10 @@ bool pick_stencil(const Geom& g, bool fp32, int nitems, bool latency,
                   int want_cluster, int want_threads, StencilCfg* out,
                   char* why, int why_len);
 
+// Every launchable configuration (FP32 tiles when fp32, else the FP64
+// kernel), at most maxn, for the autotuner.
+int list_stencil_cfgs(const Geom& g, bool fp32, int nitems, StencilCfg* out, int maxn);
+
 // Fused stencil: every item advances `steps` RK4/Euler steps of size dt
 // inside one launch, the slice resident in the cluster's shared memory.
 cudaError_t launch_stencil_fused(const Geom& g, const Coef& c, bool fp32,

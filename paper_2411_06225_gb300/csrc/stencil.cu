@@ -301,6 +301,32 @@ static bool pick_one(const Geom& g, bool fp32, int nitems, bool latency, int wan
   return true;
 }
 
+int list_stencil_cfgs(const Geom& g, bool fp32, int nitems, StencilCfg* out, int maxn) {
+  int n = 0;
+  for (int CS = 1; CS <= 16 && n < maxn; ++CS) {
+    if (g.outer % CS) continue;
+    if (fp32) {
+      // every spill-free FP32 tile at this cluster size
+      const int pxs[] = {2, 4};
+      const int rss[] = {1, 2, 4, 5, 8};
+      for (int PX : pxs)
+        for (int RS : rss) {
+          if (n >= maxn) break;
+          if (g.nx % PX || (g.outer / CS) % RS) continue;
+          const long long t = (g.plane / PX) * ((g.outer / CS) / RS);
+          StencilCfg c;
+          if (t >= 32 && t <= 512 && try_cfg(g, true, CS, (int)t, nitems, &c) && c.px == PX &&
+              c.rs == RS)
+            out[n++] = c;
+        }
+    } else {
+      StencilCfg c;
+      if (try_cfg(g, false, CS, 0, nitems, &c)) out[n++] = c;
+    }
+  }
+  return n;
+}
+
 cudaError_t launch_stencil_fused(const Geom& g, const Coef& c, bool fp32, int scheme,
                                  int steps, double dt, const double* in, double* out,
                                  double* out2, const Items& it, const StencilCfg& cfg,

@@ -443,8 +443,13 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
       const float* Bq = B + q * ncell + o * plane;
-      ew[q] = Bq[woff];
-      ee[q] = Bq[eoff];
+      // x neighbours: aligned vector loads of the adjacent tiles (lanes read
+      // consecutive vectors, so there is no bank conflict); keep the edge
+      float vw[PX], ve[PX];
+      ld_vec<PX>(Bq + woff, vw);
+      ld_vec<PX>(Bq + eoff, ve);
+      ew[q] = vw[PX - 1];
+      ee[q] = ve[0];
       if (DIMS == 3) {
         ld_vec<PX>(Bq + yn_off, yn[q]);
         ld_vec<PX>(Bq + ys_off, ys[q]);
@@ -537,7 +542,8 @@ __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant_
   const int xe = x0 + PX == nx ? 0 : x0 + PX;
   const int yn_off = (DIMS == 3 ? ((yrow + 1 == ny ? 0 : yrow + 1) * nx) : 0) + x0;
   const int ys_off = (DIMS == 3 ? ((yrow == 0 ? ny - 1 : yrow - 1) * nx) : 0) + x0;
-  const int woff = yrow * nx + xw, eoff = yrow * nx + xe;
+  // first cells of the tiles west and east of this one (periodic in x)
+  const int woff = yrow * nx + (xw + 1 - PX), eoff = yrow * nx + xe;
 
   const long long base = (long long)rank * ncell;
   const double* in = P.in + item_off(P.it.src_off, P.it.src_base, P.it.src_stride, item) + base;

@@ -127,3 +127,20 @@ def test_full_size_benchmark_workload_sampled(R, orc):
     for i in (5, 40, 64):
         r = np.abs(U[i] - orc.fine(p, U[i - 1])).max()
         assert r <= 10 * cfg["tol"], (i, r)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_autotuned_tiling_gives_the_same_results(R, precision):
+    cfg = W.config("diffreact2d", nx=64, ny=64, N=8, nF=60, tN=0.5)
+    u0 = W.initial_condition(cfg)
+    starts = np.stack([u0[0] * (1 + 0.01 * j) for j in range(cfg["N"])])[None]
+    outs = []
+    for tune in (0, 1):
+        with R.Solver(R.problem(cfg, precision=precision, autotune=tune)) as s:
+            conf = s.stencil_config("fine")
+            assert conf["tuned"] == bool(tune)
+            outs.append(host(s.fine_batch(dev(starts))))
+    if precision == "fp64":
+        assert np.array_equal(outs[0], outs[1])
+    else:
+        assert rel(outs[1], outs[0]) <= 2e-7
