@@ -121,6 +121,24 @@ def dist_env():
     return ws, rank, local
 
 
+def replica_seed(rank: int) -> int:
+    """Seed of the replica a rank solves (weak scaling: one solve per rank)."""
+    return W.CONFIGS[WORKLOAD]["seed"] + 1000 * rank
+
+
+def aggregate(t_local: float, work_local: float, dist=None, device=None):
+    """Whole-job (time, work): the max over ranks of the timed seconds and the
+    sum over ranks of the work; no other cross-rank traffic."""
+    if dist is None:
+        return t_local, work_local
+    import torch
+    tt = torch.tensor([t_local], dtype=torch.float64, device=device)
+    ww = torch.tensor([work_local], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    dist.all_reduce(ww, op=dist.ReduceOp.SUM)
+    return tt.item(), ww.item()
+
+
 def cpu_baseline(seconds_hint: float = 20.0) -> dict:
     """The FP64 oracle on the host cores: a bounded sample of the same
     workload (same grid, slices and coarse solver; nF cut to 40 of 2000
@@ -180,7 +198,7 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     rnp.lib()
-    cfg = W.config(WORKLOAD, seed=W.CONFIGS[WORKLOAD]["seed"] + 1000 * rank)
+    cfg = W.config(WORKLOAD, seed=replica_seed(rank))
     d = W.dim(cfg)
     N = cfg["N"]
     u0_h = torch.as_tensor(W.initial_condition(cfg)).pin_memory()
@@ -226,13 +244,7 @@ def run_gpu(args):
     clk = clocks.stop()
     t_sum = sum(tts) / 1e3
     # max over ranks of the timed device time, sum of the work
-    t_max, cells_all = t_sum, cells
-    if dist is not None:
-        tt = torch.tensor([t_sum], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        cc = torch.tensor([float(cells)], device=dev, dtype=torch.float64)
-        dist.all_reduce(cc, op=dist.ReduceOp.SUM)
-        t_max, cells_all = tt.item(), cc.item()
+    t_max, cells_all = aggregate(t_sum, float(cells), dist, dev)
     value = cells_all / t_max
 
     # e2e: host buffers in, result back to host, through the same C ABI
