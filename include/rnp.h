@@ -192,6 +192,27 @@ rnp_status rnp_solve(rnp_ctx* ctx, const double* u0, double* U, rnp_stats* stats
  * for errors raised by rnp_create. */
 const char* rnp_last_error(const rnp_ctx* ctx);
 
+/* --- Alg. 1 one iteration at a time (continuous batching) --------------- */
+/* The B members of a context are slots: a member can start while others
+ * are iterating, every rnp_iterate advances all active members by one
+ * iteration of Alg. 1 (their fine steps share one launch), and a finished
+ * member's slot is reused after its result is read.  rnp_solve is these
+ * calls for all members at once.                                          */
+enum { RNP_MEMBER_FREE = 0, RNP_MEMBER_ACTIVE = 1, RNP_MEMBER_CONVERGED = 2,
+       RNP_MEMBER_NOTCONV = 3 };
+/* Start a member from u0 (device [d]): the k = 0 coarse sweep of Alg. 1
+ * and the member's scaling; empties its dataset.  RNP_EBUSY if the member
+ * is active.  Returns after the sweep. */
+rnp_status rnp_member_start(rnp_ctx* ctx, int member, const double* u0);
+/* One iteration for every active member; *active receives how many are
+ * still iterating (host, may be NULL).  Returns after the iteration.     */
+rnp_status rnp_iterate(rnp_ctx* ctx, int* active);
+/* Host out: rnp_member_state state, iterations done, last converged index. */
+rnp_status rnp_member_status(const rnp_ctx* ctx, int member, int* state, int* K, int* L);
+/* Copy a finished member's U_0..U_N (device [N+1][d]) and free the slot.
+ * RNP_OK (converged) or RNP_ENOTCONV (max_iters reached).                 */
+rnp_status rnp_member_result(rnp_ctx* ctx, int member, double* U);
+
 /* --- inspection helpers (not steps of the method) ----------------------- */
 
 /* Copy the random weights of Alg. 3 to device buffers A [M][d], zeta [M]. */

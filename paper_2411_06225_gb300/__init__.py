@@ -29,6 +29,7 @@ PDE = {"burgers1d": 0, "diffreact2d": 1, "bruss2d": 2, "bruss3d": 3, "swe2d": 4,
        "heat": 5, "advect1d": 6}
 MAX_BATCH = 64
 MAX_M = 32
+RNP_MEMBER_FREE, RNP_MEMBER_ACTIVE, RNP_MEMBER_CONVERGED, RNP_MEMBER_NOTCONV = 0, 1, 2, 3
 
 
 class RnpError(RuntimeError):
@@ -140,6 +141,11 @@ def lib() -> C.CDLL:
         "rnp_get_pairs": (C.c_int, [vp, C.POINTER(C.c_longlong)]),
         "rnp_dim": (C.c_longlong, [C.POINTER(Problem)]),
         "rnp_stencil_config": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int)]),
+        "rnp_member_start": (C.c_int, [vp, C.c_int, dp]),
+        "rnp_iterate": (C.c_int, [vp, C.POINTER(C.c_int)]),
+        "rnp_member_status": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                        C.POINTER(C.c_int)]),
+        "rnp_member_result": (C.c_int, [vp, C.c_int, dp]),
         "rnp_randnet_predict_noalloc": (C.c_int, [
             C.POINTER(Problem), dp, dp, dp, dp, dp, C.c_int, C.POINTER(C.c_double),
             C.POINTER(C.c_double), dp, dp, dp, vp]),
@@ -250,6 +256,28 @@ class Solver:
             return U, st.as_dict(self.B)
         self._check(rc)
         return U, st.as_dict(self.B)
+
+    # --- Alg. 1 one iteration at a time (continuous batching) ---------------
+    def member_start(self, member: int, u0):
+        self._check(lib().rnp_member_start(self._ctx, member, _ptr(u0, shape=(self.d,))))
+
+    def iterate(self) -> int:
+        n = C.c_int(0)
+        self._check(lib().rnp_iterate(self._ctx, C.byref(n)))
+        return n.value
+
+    def member_status(self, member: int) -> dict:
+        st, K, L = C.c_int(), C.c_int(), C.c_int()
+        self._check(lib().rnp_member_status(self._ctx, member, C.byref(st), C.byref(K),
+                                            C.byref(L)))
+        return dict(state=st.value, K=K.value, L=L.value)
+
+    def member_result(self, member: int, U=None, check: bool = True):
+        U = self._empty(self.N + 1, self.d) if U is None else U
+        rc = lib().rnp_member_result(self._ctx, member, _ptr(U, shape=(self.N + 1, self.d)))
+        if not (rc == RNP_ENOTCONV and not check):
+            self._check(rc)
+        return U
 
     # --- inspection ------------------------------------------------------
     def weights(self):

@@ -61,6 +61,11 @@ struct rnp_ctx {
   unsigned long long* h_err = nullptr;  // pinned (B * (N+1))
   int* h_flags = nullptr;         // pinned (4)
   std::vector<int> P;             // pairs per member
+  // per-member iteration state (Alg. 1 split per iteration)
+  std::vector<int> mL, mK, mstate;
+  int* d_mask = nullptr;          // device [B] member mask
+  int* h_mask = nullptr;          // pinned [B]
+  rnp_stats run{};                // statistics accumulated since the last reset
   bool weights_ready = false, scaling_ready = false;
   double h_c[RNP_MAX_BATCH * 3], h_r[RNP_MAX_BATCH * 3];
 
@@ -170,7 +175,8 @@ void destroy_buffers(rnp_ctx* c) {
   void* bufs[] = {c->U, c->Fv, c->Gc, c->Yv, c->gbuf, c->qbuf, c->phic, c->phiq, c->Sds,
                   c->Yds, c->Phi, c->A, c->zeta, c->sc, c->sr, c->scale_work, c->feat_part,
                   c->nn_part, c->dist, c->alpha, c->idx, c->meff, c->flags, c->dP, c->err,
-                  c->plain_work, c->d_items, c->d_app, c->d_gate, c->A32, c->S32, c->q32};
+                  c->plain_work, c->d_items, c->d_app, c->d_gate, c->A32, c->S32, c->q32,
+                  c->d_mask};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->h_items) cudaFreeHost(c->h_items);
@@ -178,6 +184,7 @@ void destroy_buffers(rnp_ctx* c) {
   if (c->h_gate) cudaFreeHost(c->h_gate);
   if (c->h_err) cudaFreeHost(c->h_err);
   if (c->h_flags) cudaFreeHost(c->h_flags);
+  if (c->h_mask) cudaFreeHost(c->h_mask);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   if (c->evf) cudaEventDestroy(c->evf);
@@ -457,6 +464,9 @@ rnp_status rnp_create(const rnp_problem* prob, void* cuda_stream, rnp_ctx** out)
   if (prob->max_pairs > 0) cap = prob->max_pairs;
   c->cap = cap;
   c->P.assign(c->B, 0);
+  c->mL.assign(c->B, 0);
+  c->mK.assign(c->B, 0);
+  c->mstate.assign(c->B, RNP_MEMBER_FREE);
   const int B = c->B, N = c->N, M = c->M;
   const long long d = c->d;
   char why[256] = {0};
@@ -515,6 +525,8 @@ rnp_status rnp_create(const rnp_problem* prob, void* cuda_stream, rnp_ctx** out)
   ok &= dalloc(&c->d_items, (size_t)4 * c->itemcap) == cudaSuccess;
   ok &= dalloc(&c->d_app, (size_t)3 * c->itemcap) == cudaSuccess;
   ok &= dalloc(&c->d_gate, (size_t)(N + 1) * B) == cudaSuccess;
+  ok &= dalloc(&c->d_mask, (size_t)B) == cudaSuccess;
+  ok &= cudaMallocHost((void**)&c->h_mask, sizeof(int) * B) == cudaSuccess;
   ok &= cudaMallocHost((void**)&c->h_items, sizeof(long long) * 4 * c->itemcap) == cudaSuccess;
   ok &= cudaMallocHost((void**)&c->h_app, sizeof(int) * 3 * c->itemcap) == cudaSuccess;
   ok &= cudaMallocHost((void**)&c->h_gate, sizeof(int) * (N + 1) * B) == cudaSuccess;
@@ -751,7 +763,7 @@ rnp_status rnp_coarse_sweep(rnp_ctx* c, int first, const double* U_first, double
   }
   if (first == 0 && !use_fhat && c->p.scale_mode == RNP_SCALE_MINMAX) {
     CK(launch_scaling(c->g, U, sb, c->N + 1, c->B, false, c->sc, c->sr, c->scale_work,
-                      c->flags + 2, c->st));
+                      c->flags + 2, nullptr, c->st));
     c->scaling_ready = true;
   }
   int esc, fl, nf;
@@ -761,62 +773,80 @@ rnp_status rnp_coarse_sweep(rnp_ctx* c, int first, const double* U_first, double
   return RNP_OK;
 }
 
-rnp_status rnp_solve(rnp_ctx* c, const double* u0, double* Uout, rnp_stats* stats) {
-  if (!c) return RNP_EINVAL;
-  c->msg.clear();
-  if (!u0 || !Uout) return fail(c, RNP_EINVAL, "bad arguments");
-  DevGuard gd(c->dev);
-  StreamJoin sj(c);
-  auto t_start = std::chrono::steady_clock::now();
-  const long long launches0 = launches_total();
-  const int B = c->B, N = c->N, M = c->M;
+}  // extern "C"
+
+namespace {
+
+// k = 0 of Alg. 1 for the members with want[b]: U_b,0 = u0 (row b of u0,
+// member stride u0_bstride), U_b,i = G(U_b,i-1) for i = 1..N with the G values
+// kept for the first targets, then the member's scaling.  The members become
+// active with an empty dataset.
+rnp_status start_members(rnp_ctx* c, const std::vector<int>& want, const double* u0,
+                         long long u0_bstride, rnp_stats* st) {
+  const int B = c->B, N = c->N;
   const long long d = c->d, sb = (long long)(N + 1) * d, nb = (long long)N * d;
-  rnp_stats st;
-  memset(&st, 0, sizeof(st));
   rnp_status s;
   float ms;
-
-  std::fill(c->P.begin(), c->P.end(), 0);
+  for (int b = 0; b < B; ++b) {
+    c->h_mask[b] = want[b] ? 1 : 0;
+    if (want[b]) c->P[b] = 0;
+  }
   if ((s = upload_P(c))) return s;
+  CK(cudaMemcpyAsync(c->d_mask, c->h_mask, sizeof(int) * B, cudaMemcpyHostToDevice, c->st));
   CK(cudaMemsetAsync(c->flags, 0, sizeof(int) * 4, c->st));
-
-  // k = 0: U_i^0 = G(U_{i-1}^0), G values kept for the first targets.
-  CK(cudaMemcpy2DAsync(c->U, sizeof(double) * sb, u0, sizeof(double) * d, sizeof(double) * d, B,
-                       cudaMemcpyDeviceToDevice, c->st));
+  for (int b = 0; b < B; ++b)
+    if (want[b])
+      CK(cudaMemcpyAsync(c->U + (long long)b * sb, u0 + (long long)b * u0_bstride,
+                         sizeof(double) * d, cudaMemcpyDeviceToDevice, c->st));
   CK(cudaEventRecord(c->ev[0], c->st));
   for (int i = 1; i <= N; ++i) {
-    Items it = affine(B, (long long)(i - 1) * d, sb, (long long)i * d, sb, nullptr);
+    Items it = affine(B, (long long)(i - 1) * d, sb, (long long)i * d, sb, c->d_mask);
     it.dst2_base = (long long)(i - 1) * d;
     it.dst2_stride = nb;
     if ((s = run_stencil(c, false, c->U, c->U, c->Gc, it))) return s;
   }
   CK(launch_scaling(c->g, c->U, sb, N + 1, B, c->p.scale_mode == RNP_SCALE_NONE, c->sc, c->sr,
-                    c->scale_work, c->flags + 2, c->st));
+                    c->scale_work, c->flags + 2, c->d_mask, c->st));
   c->scaling_ready = true;
   if (c->randnet && (s = ensure_weights(c))) return s;
   CK(cudaEventRecord(c->ev[1], c->st));
   CK(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->st));
-  CK(cudaEventSynchronize(c->ev[1]));
   CK(cudaStreamSynchronize(c->st));
   if (c->h_flags[2]) return fail(c, RNP_ENONFINITE, "non-finite state in the k = 0 sweep");
   CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
-  st.t_sweep_ms += ms;
+  if (st) st->t_sweep_ms += ms;
+  for (int b = 0; b < B; ++b)
+    if (want[b]) {
+      c->mL[b] = 0;
+      c->mK[b] = 0;
+      c->mstate[b] = RNP_MEMBER_ACTIVE;
+    }
+  return RNP_OK;
+}
 
-  std::vector<int> L(B, 0), done(B, 0), K(B, 0);
-  const int Kmax = std::min(c->p.max_iters, N);
-  int status = RNP_OK;
-  for (int k = 1; k <= Kmax; ++k) {
-    // ---- parallel fine step over the unconverged starts ----------------
-    int nit = 0;
-    long long* srco = c->h_items;
-    long long* dsto = c->h_items + c->itemcap;
-    long long* soff = c->h_items + 2 * c->itemcap;
-    long long* poff = c->h_items + 3 * c->itemcap;
-    int* ab = c->h_app;
-    int* aj = c->h_app + c->itemcap;
-    int* ap = c->h_app + 2 * c->itemcap;
+// One iteration of Alg. 1 for every active member: the parallel fine step
+// over all their unconverged starts (one launch), the dataset append of
+// Eq. 6, the exact leftmost slice, the sweep of Eq. 3 and the stopping rule
+// of Eq. 5.  Members may be at different iterations.
+rnp_status iterate_once(rnp_ctx* c, rnp_stats* st, int* n_active) {
+  const int B = c->B, N = c->N, M = c->M;
+  const long long d = c->d, sb = (long long)(N + 1) * d, nb = (long long)N * d;
+  rnp_status s;
+  float ms;
+  std::vector<int>& L = c->mL;
+  auto active = [&](int b) { return c->mstate[b] == RNP_MEMBER_ACTIVE; };
+  // ---- work list: first-iteration members' rows first --------------------
+  int nit = 0, nfirst = 0;
+  long long* srco = c->h_items;
+  long long* dsto = c->h_items + c->itemcap;
+  long long* soff = c->h_items + 2 * c->itemcap;
+  long long* poff = c->h_items + 3 * c->itemcap;
+  int* ab = c->h_app;
+  int* aj = c->h_app + c->itemcap;
+  int* ap = c->h_app + 2 * c->itemcap;
+  for (int pass = 0; pass < 2; ++pass)
     for (int b = 0; b < B; ++b) {
-      if (done[b]) continue;
+      if (!active(b) || (c->mK[b] == 0) != (pass == 0)) continue;
       if (c->randnet && c->P[b] + (N - L[b]) > c->cap)
         return fail(c, RNP_ENOMEM, "dataset arena full (%lld rows per member)", c->cap);
       for (int j = L[b]; j < N; ++j) {
@@ -828,112 +858,194 @@ rnp_status rnp_solve(rnp_ctx* c, const double* u0, double* Uout, rnp_stats* stat
         ab[nit] = b; aj[nit] = j; ap[nit] = p;
         ++nit;
       }
+      if (pass == 0) nfirst = nit;
     }
-    for (int i = 0; i <= N; ++i)
-      for (int b = 0; b < B; ++b) c->h_gate[i * B + b] = (!done[b] && i >= L[b] + 2) ? 1 : 0;
-    CK(cudaMemcpyAsync(c->d_items, c->h_items, sizeof(long long) * 4 * c->itemcap,
-                       cudaMemcpyHostToDevice, c->st));
-    CK(cudaMemcpyAsync(c->d_app, c->h_app, sizeof(int) * 3 * c->itemcap, cudaMemcpyHostToDevice,
-                       c->st));
-    CK(cudaMemcpyAsync(c->d_gate, c->h_gate, sizeof(int) * (N + 1) * B, cudaMemcpyHostToDevice,
-                       c->st));
-    CK(cudaMemsetAsync(c->err, 0, sizeof(unsigned long long) * B * (N + 1), c->st));
-    CK(cudaEventRecord(c->ev[0], c->st));
-    Items fit{};
-    fit.src_off = c->d_items;
-    fit.dst_off = c->d_items + c->itemcap;
-    fit.n = nit;
-    if ((s = run_stencil(c, true, c->U, c->Fv, nullptr, fit))) return s;
-    CK(cudaEventRecord(c->ev[1], c->st));
-    for (int b = 0; b < B; ++b)
-      if (!done[b]) st.fine_cell_updates += (long long)(N - L[b]) * c->p.nF * d;
-
-    // ---- dataset append (Eq. 6) and features of the new rows -----------
-    AppendItems ai{c->d_app, c->d_app + c->itemcap, c->d_app + 2 * c->itemcap, nit};
-    CK(launch_append(c->g, c->U, sb, c->Fv, c->Gc, nb, c->Yv, c->fp32 ? nullptr : c->Sds,
-                     c->fp32 ? c->S32 : nullptr, c->Yds, c->cap, c->sc,
-                     c->sr, ai, c->randnet, c->st));
-    if (c->randnet) {
-      if (k == 1) {
-        Rows srows{c->d_items + 2 * c->itemcap, 0, 0};
-        Rows prow{c->d_items + 3 * c->itemcap, 0, 0};
-        if (c->fp32)
-          CK(launch_features32(c->A32, c->zeta, M, d, c->S32, srows, nit, c->Phi, prow,
-                               c->feat_part, nullptr, c->st));
-        else
-          CK(launch_features64(c->A, c->zeta, M, d, c->Sds, srows, nit, c->Phi, prow,
-                               c->feat_part, nullptr, c->st));
-      } else {
-        CK(launch_copy_phi(c->phic, (long long)N * M, c->Phi, c->cap, M, ai, c->st));
-      }
-      for (int b = 0; b < B; ++b)
-        if (!done[b]) c->P[b] += N - L[b];
-      for (int b = 0; b < B; ++b) c->h_flags[4 + b] = c->P[b];
-      CK(cudaMemcpyAsync(c->dP, c->h_flags + 4, sizeof(int) * B, cudaMemcpyHostToDevice, c->st));
+  if (nit == 0) { *n_active = 0; return RNP_OK; }
+  for (int i = 0; i <= N; ++i)
+    for (int b = 0; b < B; ++b) c->h_gate[i * B + b] = (active(b) && i >= L[b] + 2) ? 1 : 0;
+  CK(cudaMemcpyAsync(c->d_items, c->h_items, sizeof(long long) * 4 * c->itemcap,
+                     cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->d_app, c->h_app, sizeof(int) * 3 * c->itemcap, cudaMemcpyHostToDevice,
+                     c->st));
+  CK(cudaMemcpyAsync(c->d_gate, c->h_gate, sizeof(int) * (N + 1) * B, cudaMemcpyHostToDevice,
+                     c->st));
+  CK(cudaMemsetAsync(c->err, 0, sizeof(unsigned long long) * B * (N + 1), c->st));
+  CK(cudaMemsetAsync(c->flags, 0, sizeof(int) * 4, c->st));
+  // ---- parallel fine step --------------------------------------------------
+  CK(cudaEventRecord(c->ev[0], c->st));
+  Items fit{};
+  fit.src_off = c->d_items;
+  fit.dst_off = c->d_items + c->itemcap;
+  fit.n = nit;
+  if ((s = run_stencil(c, true, c->U, c->Fv, nullptr, fit))) return s;
+  CK(cudaEventRecord(c->ev[1], c->st));
+  for (int b = 0; b < B; ++b)
+    if (active(b)) st->fine_cell_updates += (long long)(N - L[b]) * c->p.nF * d;
+  // ---- dataset append (Eq. 6) and features of the new rows -----------------
+  AppendItems ai{c->d_app, c->d_app + c->itemcap, c->d_app + 2 * c->itemcap, nit};
+  CK(launch_append(c->g, c->U, sb, c->Fv, c->Gc, nb, c->Yv, c->fp32 ? nullptr : c->Sds,
+                   c->fp32 ? c->S32 : nullptr, c->Yds, c->cap, c->sc, c->sr, ai, c->randnet,
+                   c->st));
+  if (c->randnet) {
+    if (nfirst > 0) {  // first iteration: features of the k = 0 starts
+      Rows srows{c->d_items + 2 * c->itemcap, 0, 0};
+      Rows prow{c->d_items + 3 * c->itemcap, 0, 0};
+      if (c->fp32)
+        CK(launch_features32(c->A32, c->zeta, M, d, c->S32, srows, nfirst, c->Phi, prow,
+                             c->feat_part, nullptr, c->st));
+      else
+        CK(launch_features64(c->A, c->zeta, M, d, c->Sds, srows, nfirst, c->Phi, prow,
+                             c->feat_part, nullptr, c->st));
     }
-    // ---- exact leftmost slice: U_{L+1} = F(U_L) ------------------------
-    for (int b = 0; b < B; ++b)
-      if (!done[b])
-        CK(cudaMemcpyAsync(c->U + (long long)b * sb + (long long)(L[b] + 1) * d,
-                           c->Fv + (long long)b * nb + (long long)L[b] * d, sizeof(double) * d,
-                           cudaMemcpyDeviceToDevice, c->st));
-    CK(cudaEventRecord(c->ev[2], c->st));
-
-    // ---- sequential predictor-corrector sweep (Eq. 3) ------------------
-    int imin = N + 1;
-    for (int b = 0; b < B; ++b)
-      if (!done[b]) imin = std::min(imin, L[b] + 2);
-    if (imin <= N && (s = solve_sweep(c, imin))) return s;
-    CK(cudaEventRecord(c->ev[3], c->st));
-    CK(cudaMemcpyAsync(c->h_err, c->err, sizeof(unsigned long long) * B * (N + 1),
-                       cudaMemcpyDeviceToHost, c->st));
-    CK(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->st));
-    CK(cudaStreamSynchronize(c->st));
-    CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
-    st.t_fine_ms += ms;
-    CK(cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]));
-    st.t_fit_ms += ms;
-    CK(cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]));
-    st.t_sweep_ms += ms;
-    if (c->h_flags[1]) return fail(c, RNP_ENONFINITE, "ridge system not positive definite");
-    if (c->h_flags[2]) return fail(c, RNP_ENONFINITE, "non-finite state at iteration %d", k);
-
-    // ---- stopping rule (Eq. 5) -----------------------------------------
-    bool all = true;
-    for (int b = 0; b < B; ++b) {
-      if (done[b]) continue;
-      int Ln = L[b] + 1;
-      for (int i = L[b] + 2; i <= N; ++i) {
-        double e;
-        memcpy(&e, &c->h_err[(long long)b * (N + 1) + i], sizeof(double));
-        if (e < c->p.tol) Ln = i; else break;
-      }
-      L[b] = Ln;
-      K[b] = k;
-      if (L[b] == N) done[b] = 1;
-      all &= done[b] != 0;
+    if (nit > nfirst) {  // later iterations: the sweep already computed them
+      AppendItems rest{c->d_app + nfirst, c->d_app + c->itemcap + nfirst,
+                       c->d_app + 2 * c->itemcap + nfirst, nit - nfirst};
+      CK(launch_copy_phi(c->phic, (long long)N * M, c->Phi, c->cap, M, rest, c->st));
     }
-    if (all) break;
+    for (int b = 0; b < B; ++b)
+      if (active(b)) c->P[b] += N - L[b];
+    for (int b = 0; b < B; ++b) c->h_flags[4 + b] = c->P[b];
+    CK(cudaMemcpyAsync(c->dP, c->h_flags + 4, sizeof(int) * B, cudaMemcpyHostToDevice, c->st));
   }
-  st.lambda_escalations = c->h_flags[0];
+  // ---- exact leftmost slice: U_{L+1} = F(U_L) ------------------------------
+  for (int b = 0; b < B; ++b)
+    if (active(b))
+      CK(cudaMemcpyAsync(c->U + (long long)b * sb + (long long)(L[b] + 1) * d,
+                         c->Fv + (long long)b * nb + (long long)L[b] * d, sizeof(double) * d,
+                         cudaMemcpyDeviceToDevice, c->st));
+  CK(cudaEventRecord(c->ev[2], c->st));
+  // ---- sequential predictor-corrector sweep (Eq. 3) ------------------------
+  int imin = N + 1;
+  for (int b = 0; b < B; ++b)
+    if (active(b)) imin = std::min(imin, L[b] + 2);
+  if (imin <= N && (s = solve_sweep(c, imin))) return s;
+  CK(cudaEventRecord(c->ev[3], c->st));
+  CK(cudaMemcpyAsync(c->h_err, c->err, sizeof(unsigned long long) * B * (N + 1),
+                     cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+  st->t_fine_ms += ms;
+  CK(cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]));
+  st->t_fit_ms += ms;
+  CK(cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]));
+  st->t_sweep_ms += ms;
+  st->lambda_escalations += c->h_flags[0];
+  if (c->h_flags[1]) return fail(c, RNP_ENONFINITE, "ridge system not positive definite");
+  if (c->h_flags[2]) return fail(c, RNP_ENONFINITE, "non-finite state");
+  // ---- stopping rule (Eq. 5) -----------------------------------------------
+  const int Kmax = std::min(c->p.max_iters, N);
+  int left = 0;
+  for (int b = 0; b < B; ++b) {
+    if (!active(b)) continue;
+    int Ln = L[b] + 1;
+    for (int i = L[b] + 2; i <= N; ++i) {
+      double e;
+      memcpy(&e, &c->h_err[(long long)b * (N + 1) + i], sizeof(double));
+      if (e < c->p.tol) Ln = i; else break;
+    }
+    L[b] = Ln;
+    c->mK[b] += 1;
+    if (L[b] == N) c->mstate[b] = RNP_MEMBER_CONVERGED;
+    else if (c->mK[b] >= Kmax) c->mstate[b] = RNP_MEMBER_NOTCONV;
+    else ++left;
+  }
+  *n_active = left;
+  return RNP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rnp_status rnp_solve(rnp_ctx* c, const double* u0, double* Uout, rnp_stats* stats) {
+  if (!c) return RNP_EINVAL;
+  c->msg.clear();
+  if (!u0 || !Uout) return fail(c, RNP_EINVAL, "bad arguments");
+  DevGuard gd(c->dev);
+  StreamJoin sj(c);
+  auto t_start = std::chrono::steady_clock::now();
+  const long long launches0 = launches_total();
+  const int B = c->B, N = c->N;
+  const long long d = c->d, sb = (long long)(N + 1) * d;
+  rnp_stats st;
+  memset(&st, 0, sizeof(st));
+  rnp_status s;
+  if ((s = start_members(c, std::vector<int>(B, 1), u0, d, &st))) return s;
+  int n_active = B;
+  while (n_active > 0) {
+    s = iterate_once(c, &st, &n_active);
+    if (s != RNP_OK) return s;
+  }
   CK(cudaMemcpyAsync(Uout, c->U, sizeof(double) * B * sb, cudaMemcpyDeviceToDevice, c->st));
   CK(cudaStreamSynchronize(c->st));
   st.converged = 1;
   st.L = N;
   for (int b = 0; b < B; ++b) {
-    st.K = std::max(st.K, K[b]);
-    st.K_each[b] = K[b];
-    st.L = std::min(st.L, L[b]);
-    st.converged &= done[b];
+    st.K = std::max(st.K, c->mK[b]);
+    st.K_each[b] = c->mK[b];
+    st.L = std::min(st.L, c->mL[b]);
+    st.converged &= c->mstate[b] == RNP_MEMBER_CONVERGED;
     st.pairs += c->P[b];
+    c->mstate[b] = RNP_MEMBER_FREE;
   }
-  if (!st.converged) status = RNP_ENOTCONV;
   st.t_total_ms =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   st.kernel_launches = launches_total() - launches0;
   if (stats) *stats = st;
-  if (status == RNP_ENOTCONV) return fail(c, RNP_ENOTCONV, "not converged after %d iterations", Kmax);
+  if (!st.converged)
+    return fail(c, RNP_ENOTCONV, "not converged after %d iterations",
+                std::min(c->p.max_iters, N));
   return RNP_OK;
+}
+
+rnp_status rnp_member_start(rnp_ctx* c, int member, const double* u0) {
+  if (!c) return RNP_EINVAL;
+  c->msg.clear();
+  if (!u0 || member < 0 || member >= c->B) return fail(c, RNP_EINVAL, "bad arguments");
+  if (c->mstate[member] == RNP_MEMBER_ACTIVE)
+    return fail(c, RNP_EBUSY, "member %d is still iterating", member);
+  DevGuard gd(c->dev);
+  StreamJoin sj(c);
+  std::vector<int> want(c->B, 0);
+  want[member] = 1;
+  // member stride 0: row `member` of the source is u0 itself
+  return start_members(c, want, u0, 0, &c->run);
+}
+
+rnp_status rnp_iterate(rnp_ctx* c, int* active) {
+  if (!c) return RNP_EINVAL;
+  c->msg.clear();
+  DevGuard gd(c->dev);
+  StreamJoin sj(c);
+  int n = 0;
+  rnp_status s = iterate_once(c, &c->run, &n);
+  if (active) *active = n;
+  return s;
+}
+
+rnp_status rnp_member_status(const rnp_ctx* c, int member, int* state, int* K, int* L) {
+  if (!c || member < 0 || member >= c->B) return RNP_EINVAL;
+  if (state) *state = c->mstate[member];
+  if (K) *K = c->mK[member];
+  if (L) *L = c->mL[member];
+  return RNP_OK;
+}
+
+rnp_status rnp_member_result(rnp_ctx* c, int member, double* U) {
+  if (!c) return RNP_EINVAL;
+  c->msg.clear();
+  if (!U || member < 0 || member >= c->B) return fail(c, RNP_EINVAL, "bad arguments");
+  if (c->mstate[member] == RNP_MEMBER_ACTIVE || c->mstate[member] == RNP_MEMBER_FREE)
+    return fail(c, RNP_EINVAL, "member %d has no finished result", member);
+  DevGuard gd(c->dev);
+  StreamJoin sj(c);
+  const long long sb = (long long)(c->N + 1) * c->d;
+  CK(cudaMemcpyAsync(U, c->U + (long long)member * sb, sizeof(double) * sb,
+                     cudaMemcpyDeviceToDevice, c->st));
+  const int st = c->mstate[member];
+  c->mstate[member] = RNP_MEMBER_FREE;
+  return st == RNP_MEMBER_CONVERGED ? RNP_OK : RNP_ENOTCONV;
 }
 
 }  // extern "C"

@@ -86,10 +86,11 @@ cudaError_t launch_weights(uint64_t seed, int M, long long d, double* A, double*
 // ---------------------------------------------------------------------------
 __global__ void k_minmax_partial(const double* U, long long bstride, int nstates,
                                  long long n, long long d, int ncomp, double* work,
-                                 int nchunk, int* nonfinite) {
+                                 int nchunk, int* nonfinite, const int* mask) {
   // blockIdx.y = b * ncomp + q ; blockIdx.x = chunk
   const int bq = blockIdx.y;
   const int b = bq / ncomp, q = bq - b * ncomp;
+  if (mask && !mask[b]) return;
   const long long tot = (long long)nstates * n;
   double mn = 1.0 / 0.0, mx = -1.0 / 0.0;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
@@ -119,10 +120,11 @@ __global__ void k_minmax_partial(const double* U, long long bstride, int nstates
 }
 
 __global__ void k_minmax_finish(const double* work, int nchunk, int B, int ncomp,
-                                bool none, double* c, double* r) {
+                                bool none, double* c, double* r, const int* mask) {
   const int bq = blockIdx.x * blockDim.x + threadIdx.x;
   if (bq >= B * ncomp) return;
   const int b = bq / ncomp, q = bq - b * ncomp;
+  if (mask && !mask[b]) return;
   if (none) {
     c[b * 3 + q] = 0.0;
     r[b * 3 + q] = 1.0;
@@ -146,14 +148,14 @@ static const int kScaleChunks = 64;
 
 cudaError_t launch_scaling(const Geom& g, const double* U, long long bstride, int nstates,
                            int B, bool none, double* c, double* r, double* work,
-                           int* nonfinite, cudaStream_t st) {
+                           int* nonfinite, const int* mask, cudaStream_t st) {
   dim3 grid(kScaleChunks, B * g.ncomp);
   count_launches(1);
   k_minmax_partial<<<grid, 256, 0, st>>>(U, bstride, nstates, g.n, g.d, g.ncomp, work,
-                                         kScaleChunks, nonfinite);
+                                         kScaleChunks, nonfinite, mask);
   count_launches(1);
   k_minmax_finish<<<(B * g.ncomp + 63) / 64, 64, 0, st>>>(work, kScaleChunks, B, g.ncomp,
-                                                          none, c, r);
+                                                          none, c, r, mask);
   return cudaGetLastError();
 }
 

@@ -112,10 +112,12 @@ cudaError_t launch_weights(uint64_t seed, int M, long long d, double* A,
 // Per-member, per-species min/max over `nstates` consecutive states starting
 // at U + b * bstride, then c = (max + min) / 2, r = (max - min) / 2 (r = 1
 // when 0), written to c[b*3 + q], r[b*3 + q].  none = identity scaling.
-// nonfinite (optional) is set when a scanned value is NaN or Inf.
+// nonfinite (optional) is set when a scanned value is NaN or Inf; mask
+// (optional) restricts the update to members b with mask[b] != 0.
 cudaError_t launch_scaling(const Geom& g, const double* U, long long bstride,
                            int nstates, int B, bool none, double* c, double* r,
-                           double* work, int* nonfinite, cudaStream_t st);
+                           double* work, int* nonfinite, const int* mask,
+                           cudaStream_t st);
 
 // Rows r = 0..R-1: S[dst(r)..] = (U[src(r)..] - c[b]) / r[b] with
 // b = row_b[r] (or r / row_b_div); S (FP64) and S32 (rounded to FP32) are

@@ -1,0 +1,87 @@
+"""Continuous batching: members that join a context while others iterate,
+and the server's mixed request stream, give the same result as the same
+solve alone (bit-identical in FP64; within the FP32 stencil bound of 2e-7
+relative in mixed precision)."""
+import time
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    import paper_2411_06225_gb300 as rnp
+    rnp.build()
+    rnp.lib()
+    return rnp
+
+
+def dev(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def alone(R, cfg, u0, precision):
+    with R.Solver(R.problem(dict(cfg, batch=1), precision=precision)) as s:
+        U, st = s.solve(dev(u0[None]))
+        return U.cpu().numpy()[0], st["K"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_member_joining_mid_flight_equals_solving_alone(R, precision):
+    cfg = W.config("diffreact2d", nx=32, ny=32, N=12, nF=80, tN=1.0)
+    u0s = [W.initial_condition(cfg, seed=s)[0] for s in (11, 12, 13)]
+    with R.Solver(R.problem(dict(cfg, batch=2), precision=precision)) as s:
+        s.member_start(0, dev(u0s[0]))
+        s.iterate()
+        s.iterate()
+        s.member_start(1, dev(u0s[1]))           # joins while member 0 iterates
+        results = {}
+        queue = [2]
+        for _ in range(100):
+            n = s.iterate()
+            for m in (0, 1):
+                st = s.member_status(m)
+                if st["state"] in (R.RNP_MEMBER_CONVERGED, R.RNP_MEMBER_NOTCONV):
+                    assert st["state"] == R.RNP_MEMBER_CONVERGED
+                    U = s.member_result(m).cpu().numpy()
+                    results[len(results)] = (U, st["K"])
+                    if queue:                    # the freed slot takes a new request
+                        s.member_start(m, dev(u0s[queue.pop()]))
+            if n == 0 and not queue and s.member_status(0)["state"] == R.RNP_MEMBER_FREE \
+                    and s.member_status(1)["state"] == R.RNP_MEMBER_FREE:
+                break
+    assert len(results) == 3
+    refs = [alone(R, cfg, u, precision) for u in u0s]
+    for U, K in results.values():
+        errs = [np.abs(U - r[0]).max() / np.abs(r[0]).max() for r in refs]
+        j = int(np.argmin(errs))
+        if precision == "fp64":
+            assert errs[j] == 0.0 and K == refs[j][1]
+        else:
+            assert errs[j] <= 2e-7 and abs(K - refs[j][1]) <= 1
+
+
+def test_server_stream_results_equal_their_solo_solves(R):
+    from paper_2411_06225_gb300.serve import Server
+    reqs = []
+    for k, (g, N) in enumerate([(32, 8), (32, 8), (64, 8), (32, 8), (64, 8), (32, 16)]):
+        cfg = W.config("swe2d", nx=g, ny=g, N=N, nF=0, nG=0, seed=100 + k, max_iters=8)
+        reqs.append(cfg)
+    srv = Server(precision="fp64", slots=2, reserve_bytes=1 << 30)
+    srv.start()
+    futs = []
+    for cfg in reqs:
+        futs.append(srv.submit(cfg, W.initial_condition(cfg)[0]))
+        time.sleep(0.01)                            # arrivals while others run
+    out = [f.result(timeout=300) for f in futs]
+    srv.stop()
+    assert srv.turns > 0
+    for cfg, res in zip(reqs, out):
+        ref, K = alone(R, dict(cfg, seed=srv.weight_seed), W.initial_condition(cfg)[0], "fp64")
+        assert res["converged"] and res["K"] == K
+        assert np.array_equal(res["U"], ref)
