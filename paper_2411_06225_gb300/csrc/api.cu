@@ -324,9 +324,12 @@ rnp_status sweep_step(rnp_ctx* c, double* U, long long ubs, int i, double* Gc,
   return RNP_OK;
 }
 
-// The solve's sweep i = i0 .. N.  In the fused path it is captured once per
-// i0 as a CUDA graph (every pointer is fixed per context; the gate table and
-// the dataset size are read from device memory) and replayed afterwards.
+// The solve's sweep i = i0 .. N.  In the fused path the whole range
+// i = 2 .. N is captured once per context as a CUDA graph (every pointer is
+// fixed per context; the gate table and the dataset size are read from
+// device memory): steps below a member's L + 2 are gated off on the device,
+// so one graph serves every iteration and every mix of members.  Steps
+// below min(L) + 2 cost one empty launch per kernel.
 rnp_status solve_sweep(rnp_ctx* c, int i0) {
   const long long sb = (long long)(c->N + 1) * c->d;
   rnp_status s;
@@ -336,6 +339,7 @@ rnp_status solve_sweep(rnp_ctx* c, int i0) {
         return s;
     return RNP_OK;
   }
+  i0 = 2;
   if (!c->sweep_graph[i0]) {
     const long long before = launches_total();
     cudaGraph_t graph = nullptr;
@@ -971,7 +975,9 @@ rnp_status rnp_solve(rnp_ctx* c, const double* u0, double* Uout, rnp_stats* stat
   rnp_stats st;
   memset(&st, 0, sizeof(st));
   rnp_status s;
-  if ((s = start_members(c, std::vector<int>(B, 1), u0, d, &st))) return s;
+  const std::vector<int> all(B, 1);
+  s = start_members(c, all, u0, d, &st);
+  if (s != RNP_OK) return s;
   int n_active = B;
   while (n_active > 0) {
     s = iterate_once(c, &st, &n_active);

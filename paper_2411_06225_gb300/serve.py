@@ -20,11 +20,10 @@ turn, without waiting for the others to finish.
 from __future__ import annotations
 
 import ctypes as C
-import math
 import queue
 import threading
 import time
-from concurrent.futures import Future, ThreadPoolExecutor
+from concurrent.futures import Future
 
 import numpy as np
 
@@ -60,9 +59,11 @@ class Request:
 
 
 class Pool:
-    """One class of requests: a context with `slots` members and its stream."""
+    """One class of requests: a context with `slots` members, its stream and
+    its own serving thread (admit -> iterate -> complete), so that pools of
+    different classes advance independently and overlap on the GPU."""
 
-    def __init__(self, cfg, slots, precision, weight_seed):
+    def __init__(self, cfg, slots, precision, weight_seed, server):
         import torch
         self.cfg = dict(cfg, batch=slots, seed=weight_seed)
         self.stream = torch.cuda.Stream()
@@ -72,6 +73,13 @@ class Pool:
         self.members = [None] * slots
         self.d = self.solver.d
         self.N = self.cfg["N"]
+        self.queue: "queue.Queue[Request]" = queue.Queue()
+        self.server = server
+        self.iterations = 0
+        self.idle_since = time.perf_counter()
+        self._stop = threading.Event()
+        self.thread = threading.Thread(target=self._loop, daemon=True)
+        self.thread.start()
 
     def free_slot(self):
         for i, r in enumerate(self.members):
@@ -79,29 +87,29 @@ class Pool:
                 return i
         return None
 
-    def start(self, slot, req):
+    def busy(self):
+        return any(r is not None for r in self.members) or not self.queue.empty()
+
+    def _start(self, slot, req):
         import torch
         with torch.cuda.stream(self.stream):
             u0 = torch.as_tensor(np.ascontiguousarray(req.u0, np.float64), device="cuda")
             st = lib().rnp_member_start(self.solver._ctx, slot, C.c_void_p(u0.data_ptr()))
-            self.stream.synchronize()
         if st != RNP_OK:
             raise RnpError(st, lib().rnp_last_error(self.solver._ctx).decode())
         self.members[slot] = req
+        req.t_admit = time.perf_counter()
 
-    def iterate(self):
+    def _iterate(self):
         n = C.c_int(0)
         st = lib().rnp_iterate(self.solver._ctx, C.byref(n))
         if st != RNP_OK:
             raise RnpError(st, lib().rnp_last_error(self.solver._ctx).decode())
+        self.iterations += 1
         return n.value
 
-    def active(self):
-        return any(r is not None for r in self.members)
-
-    def collect(self):
+    def _collect(self):
         import torch
-        done = []
         for slot, req in enumerate(self.members):
             if req is None:
                 continue
@@ -115,15 +123,54 @@ class Pool:
                 lib().rnp_member_result(self.solver._ctx, slot, C.c_void_p(U.data_ptr()))
                 Uh = U.cpu()
             self.members[slot] = None
-            done.append((req, Uh.numpy(), K.value, state.value == RNP_MEMBER_CONVERGED))
-        return done
+            req.t_done = time.perf_counter()
+            self.server._completed(req, dict(id=req.id, U=Uh.numpy(), K=K.value,
+                                             converged=state.value == RNP_MEMBER_CONVERGED,
+                                             latency=req.t_done - req.arrival))
+
+    def _loop(self):
+        try:
+            while not self._stop.is_set():
+                # admit queued requests into free slots (they join mid-flight)
+                while True:
+                    slot = self.free_slot()
+                    if slot is None:
+                        break
+                    try:
+                        req = self.queue.get_nowait()
+                    except queue.Empty:
+                        break
+                    self._start(slot, req)
+                if any(r is not None for r in self.members):
+                    self._iterate()
+                    self._collect()
+                    self.idle_since = time.perf_counter()
+                else:
+                    try:
+                        req = self.queue.get(timeout=0.002)
+                        self.queue.put(req)
+                    except queue.Empty:
+                        pass
+        except Exception as e:  # fail this pool's requests; the server goes on
+            for r in self.members:
+                if r is not None and not r.future.done():
+                    r.future.set_exception(e)
+            while not self.queue.empty():
+                r = self.queue.get_nowait()
+                if not r.future.done():
+                    r.future.set_exception(e)
 
     def close(self):
+        self._stop.set()
+        self.thread.join()
         self.solver.close()
 
 
 class Server:
-    """Continuous-batching server; see the module docstring."""
+    """Continuous-batching server; see the module docstring.  A dispatcher
+    thread routes arrivals to their class's pool, creating a pool while free
+    HBM covers it plus a reserve (otherwise the request waits, and idle pools
+    are released to make room)."""
 
     def __init__(self, precision: str = "mixed", slots: int = 4,
                  reserve_bytes: int = 8 << 30, weight_seed: int = 2415, max_pools: int = 16):
@@ -135,22 +182,31 @@ class Server:
         self.pools: dict = {}
         self.waiting: list = []
         self.inbox: "queue.Queue[Request]" = queue.Queue()
-        self.exec = ThreadPoolExecutor(max_workers=max_pools)
         self._stop = threading.Event()
         self._thread = None
+        self._lock = threading.Lock()
         self.completed = 0
-        self.turns = 0
         self.next_id = 0
 
-    # -- client side ---------------------------------------------------------
+    @property
+    def turns(self):
+        return sum(p.iterations for p in self.pools.values())
+
     def submit(self, cfg: dict, u0: np.ndarray, arrival: float | None = None) -> Future:
-        req = Request(self.next_id, cfg, u0, time.perf_counter() if arrival is None else arrival)
-        self.next_id += 1
+        with self._lock:
+            rid = self.next_id
+            self.next_id += 1
+        req = Request(rid, cfg, u0, time.perf_counter() if arrival is None else arrival)
         self.inbox.put(req)
         return req.future
 
+    def _completed(self, req, result):
+        with self._lock:
+            self.completed += 1
+        req.future.set_result(result)
+
     def start(self):
-        self._thread = threading.Thread(target=self._loop, daemon=True)
+        self._thread = threading.Thread(target=self._dispatch, daemon=True)
         self._thread.start()
 
     def stop(self):
@@ -159,16 +215,9 @@ class Server:
             self._thread.join()
         for p in self.pools.values():
             p.close()
-        self.exec.shutdown()
 
-    # -- serving loop ----------------------------------------------------------
-    def _admit(self):
+    def _route(self):
         import torch
-        while True:
-            try:
-                self.waiting.append(self.inbox.get_nowait())
-            except queue.Empty:
-                break
         still = []
         for req in self.waiting:
             key = class_key(req.cfg)
@@ -177,54 +226,31 @@ class Server:
                 need = pool_bytes(req.cfg, self.slots, self.precision)
                 free, _ = torch.cuda.mem_get_info()
                 if len(self.pools) >= self.max_pools or free - need < self.reserve:
-                    still.append(req)          # no memory for a new class yet
+                    idle = [k for k, p in self.pools.items()
+                            if not p.busy() and time.perf_counter() - p.idle_since > 0.05]
+                    if idle:
+                        self.pools.pop(idle[0]).close()
+                    still.append(req)
                     continue
-                pool = self.pools[key] = Pool(req.cfg, self.slots, self.precision,
-                                              self.weight_seed)
-            slot = pool.free_slot()
-            if slot is None:
-                still.append(req)
-                continue
-            try:
-                pool.start(slot, req)
-                req.t_admit = time.perf_counter()
-            except RnpError as e:
-                req.future.set_exception(e)
+                try:
+                    pool = self.pools[key] = Pool(req.cfg, self.slots, self.precision,
+                                                  self.weight_seed, self)
+                except RnpError as e:
+                    req.future.set_exception(e)
+                    continue
+            pool.queue.put(req)
         self.waiting = still
 
-    def _turn(self):
-        self._admit()
-        busy = [p for p in self.pools.values() if p.active()]
-        if not busy:
-            return False
-        list(self.exec.map(lambda p: p.iterate(), busy))
-        for p in busy:
-            for req, U, K, conv in p.collect():
-                req.t_done = time.perf_counter()
-                self.completed += 1
-                req.future.set_result(dict(id=req.id, U=U, K=K, converged=conv,
-                                           latency=req.t_done - req.arrival))
-        # drop idle pools when requests wait for memory
-        if self.waiting:
-            for key in [k for k, p in self.pools.items() if not p.active()]:
-                self.pools.pop(key).close()
-        self.turns += 1
-        return True
-
-    def _loop(self):
+    def _dispatch(self):
         while not self._stop.is_set():
             try:
-                worked = self._turn()
-            except Exception as e:  # fail every outstanding request, then stop
-                for p in self.pools.values():
-                    for r in p.members:
-                        if r is not None and not r.future.done():
-                            r.future.set_exception(e)
-                for r in self.waiting:
-                    r.future.set_exception(e)
-                return
-            if not worked and self.inbox.empty() and not self.waiting:
-                time.sleep(0.0005)
+                self.waiting.append(self.inbox.get(timeout=0.002))
+                while True:
+                    self.waiting.append(self.inbox.get_nowait())
+            except queue.Empty:
+                pass
+            if self.waiting:
+                self._route()
 
 
 def run_stream(reqs: list[dict], precision: str = "mixed", slots: int = 4,
@@ -251,7 +277,7 @@ def run_stream(reqs: list[dict], precision: str = "mixed", slots: int = 4,
                 p99_ms=float(np.percentile(lat, 99)), mean_ms=float(lat.mean()),
                 solves_per_s=len(res) / (t_end - t0), converged=sum(x["converged"] for x in res),
                 K_mean=float(np.mean([x["K"] for x in res])), wall_s=t_end - t0,
-                pools=len(srv.pools), turns=srv.turns)
+                pools=len(srv.pools), iterations=srv.turns)
 
 
 def main():
