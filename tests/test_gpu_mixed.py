@@ -144,3 +144,16 @@ def test_autotuned_tiling_gives_the_same_results(R, precision):
         assert np.array_equal(outs[0], outs[1])
     else:
         assert rel(outs[1], outs[0]) <= 2e-7
+
+
+def test_large_shallow_water_grid_runs_an_fp32_tile(R, orc):
+    """256 x 256 x 3 has no spill-free FP32 tile of <= 512 threads; the mixed
+    context must still pick an FP32 tile (not the FP64 kernel)."""
+    cfg = W.config("swe2d", nx=256, ny=256, N=2, nF=40, nG=10)
+    u0 = W.initial_condition(cfg)
+    with R.Solver(R.problem(cfg, precision="mixed")) as s:
+        assert s.stencil_config("fine")["px"] > 0
+        assert s.stencil_config("coarse")["px"] > 0
+        out = host(s.fine_batch(dev(np.stack([u0[0]] * 2)[None])))
+    e = rel(out[0, 0], orc.fine(orc.problem(cfg), u0[0]))
+    assert e <= 2e-7, e
