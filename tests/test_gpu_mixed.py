@@ -149,7 +149,7 @@ def test_autotuned_tiling_gives_the_same_results(R, precision):
 def test_large_shallow_water_grid_runs_an_fp32_tile(R, orc):
     """256 x 256 x 3 has no spill-free FP32 tile of <= 512 threads; the mixed
     context must still pick an FP32 tile (not the FP64 kernel)."""
-    cfg = W.config("swe2d", nx=256, ny=256, N=2, nF=40, nG=10)
+    cfg = W.config("swe2d", nx=256, ny=256, N=64, nF=0, nG=0)   # CFL-rule step counts
     u0 = W.initial_condition(cfg)
     with R.Solver(R.problem(cfg, precision="mixed")) as s:
         assert s.stencil_config("fine")["px"] > 0
