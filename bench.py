@@ -39,16 +39,21 @@ import numpy as np  # noqa: E402
 
 import workloads as W  # noqa: E402
 
-WORKLOAD = "diffreact2d"
+WORKLOAD = "diffreact2d"  # the benchmark workload; --workload measures the others
 METRIC = ("Parareal time-to-solution @tol 1e-6 vs plain FP64; cell-updates/s, %HBM; "
           "p50/p99")
 UNIT = "cell-updates/s"
 
-# Algorithmic FP32 flops per fine cell-update (one unknown, one RK4 step) of
-# the diffusion-reaction stencil, counted from the formulas with every
-# multiply and add separate: per grid point and stage 16 (u) + 12 (v); per
-# unknown and step 13 for the stage combinations.
-FLOPS_PER_CELL_UPDATE = {"diffreact2d": (4 * (16 + 12) + 2 * 13) / 2.0}
+# Algorithmic FP32 flops per fine cell-update (one unknown, one RK4 step),
+# counted from the right-hand side formulas with every multiply and add
+# separate, plus 13 per unknown for the four stage combinations:
+#   diffusion-reaction 2D: per grid point and stage 16 (u) + 12 (v)
+#   Brusselator 2D: 16 (u) + 13 (v); 3D: 21 (u) + 18 (v)
+#   Burgers 1D: 9 per point and stage
+FLOPS_PER_CELL_UPDATE = {"diffreact2d": (4 * (16 + 12) + 2 * 13) / 2.0,
+                         "bruss2d": (4 * (16 + 13) + 2 * 13) / 2.0,
+                         "bruss3d": (4 * (21 + 18) + 2 * 13) / 2.0,
+                         "burgers1d": 4 * 9 + 13.0}
 
 
 def peaks() -> dict:
@@ -121,6 +126,13 @@ def dist_env():
     return ws, rank, local
 
 
+def describe(cfg: dict) -> str:
+    grid = "x".join(str(v) for v in (cfg["nx"], cfg["ny"], cfg["nz"]) if v > 1)
+    return (f"{cfg['pde']} {grid}x{W.ncomp(cfg)} periodic, N={cfg['N']}, "
+            f"F=RK4x{cfg['nF']}, G=Eulerx{cfg['nG']}, M={cfg['M']}, m={cfg['m']}, "
+            f"tol={cfg['tol']}, batch={cfg.get('batch', 1)}, max_iters={cfg['max_iters']}")
+
+
 def replica_seed(rank: int) -> int:
     """Seed of the replica a rank solves (weak scaling: one solve per rank)."""
     return W.CONFIGS[WORKLOAD]["seed"] + 1000 * rank
@@ -190,6 +202,8 @@ def run_reference(args):
 def run_gpu(args):
     import torch
     import paper_2411_06225_gb300 as rnp
+    global WORKLOAD
+    WORKLOAD = args.workload
     ws, rank, local = dist_env()
     dist = None
     if ws > 1:
@@ -199,6 +213,8 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     rnp.lib()
     cfg = W.config(WORKLOAD, seed=replica_seed(rank))
+    if args.max_iters:
+        cfg["max_iters"] = args.max_iters
     d = W.dim(cfg)
     N = cfg["N"]
     u0_h = torch.as_tensor(W.initial_condition(cfg)).pin_memory()
@@ -248,7 +264,7 @@ def run_gpu(args):
     value = cells_all / t_max
 
     # e2e: host buffers in, result back to host, through the same C ABI
-    U_h = torch.empty((1, N + 1, d), dtype=torch.float64).pin_memory()
+    U_h = torch.empty((cfg.get("batch", 1), N + 1, d), dtype=torch.float64).pin_memory()
     e2e_t = []
     for _ in range(max(2, min(args.steps, 3))):
         flush.fill_(1.0)
@@ -292,8 +308,7 @@ def run_gpu(args):
             "ms_per_step": statistics.mean(tts), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD} 128x128x2 periodic, N=64, F=RK4x2000, "
-                                   "G=Eulerx8, M=100, m=4, tol=1e-6",
+            "config": {"workload": describe(cfg),
                        "precision": args.precision, "exec": "fused", "autotune": True,
                        "replica_per_rank": True, "l2": "flushed between timed steps "
                        "(256 MB write)", "parallelism": f"replicas x{ws}"},
@@ -338,6 +353,9 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=["diffreact2d", "burgers1d", "bruss2d", "bruss3d"])
+    ap.add_argument("--max-iters", type=int, default=0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

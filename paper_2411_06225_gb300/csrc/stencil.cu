@@ -213,7 +213,8 @@ static bool try_cfg(const Geom& g, bool fp32, int CS, int threads, int nitems,
         // relaxed pass accepts tiles that spill a little: still far faster
         // than the FP64 kernel on GB300's FP64 units)
         int budget = (g.dims <= 2 && g.ncomp <= 2) ? 16 : 8;
-        if (g_tile_relax) budget = 24;
+        if (g_tile_relax == 1) budget = 24;
+        if (g_tile_relax == 2) budget = 40;
         if (RS * g.ncomp * PX > budget) continue;
         const long long t = tiles * (nloc / RS);
         if (t > 512 || t < 1) continue;
@@ -262,11 +263,13 @@ bool pick_stencil(const Geom& g, bool fp32, int nitems, bool latency, int want_c
     g_tile_relax = 0;
     if (pick_one(g, true, nitems, latency, want_cluster, want_threads, out, why, why_len))
       return true;
-    g_tile_relax = 1;
-    const bool ok =
-        pick_one(g, true, nitems, latency, want_cluster, want_threads, out, why, why_len);
-    g_tile_relax = 0;
-    if (ok) return true;
+    for (int level = 1; level <= 2; ++level) {
+      g_tile_relax = level;
+      const bool ok =
+          pick_one(g, true, nitems, latency, want_cluster, want_threads, out, why, why_len);
+      g_tile_relax = 0;
+      if (ok) return true;
+    }
   }
   return pick_one(g, false, nitems, latency, want_cluster, want_threads, out, why, why_len);
 }
