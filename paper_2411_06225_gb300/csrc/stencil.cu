@@ -193,7 +193,7 @@ static bool launchable(FusedFn fn, int CS, int threads, size_t smem, int nitems)
 static thread_local int g_tile_relax = 0;  // 1: allow register tiles that spill a little
 
 static bool try_cfg(const Geom& g, bool fp32, int CS, int threads, int nitems,
-                    StencilCfg* out) {
+                    StencilCfg* out, int want_px = 0, int want_rs = 0) {
   if (g.outer % CS) return false;
   if (g.dims == 1 && CS != 1) return false;
   const long long nloc = g.outer / CS;
@@ -205,10 +205,10 @@ static bool try_cfg(const Geom& g, bool fp32, int CS, int threads, int nitems,
     const int pxs[] = {2, 4};
     const int rss[] = {1, 2, 4, 5, 8};
     for (int PX : pxs) {
-      if (g.nx % PX) continue;
+      if (g.nx % PX || (want_px && PX != want_px)) continue;
       const long long tiles = g.plane / PX;
       for (int RS : rss) {
-        if (nloc % RS) continue;
+        if (nloc % RS || (want_rs && RS != want_rs)) continue;
         // register tile measured spill-free with ptxas at 512 threads (the
         // relaxed pass accepts tiles that spill a little: still far faster
         // than the FP64 kernel on GB300's FP64 units)
@@ -331,8 +331,7 @@ int list_stencil_cfgs(const Geom& g, bool fp32, int nitems, StencilCfg* out, int
           if (g.nx % PX || (g.outer / CS) % RS) continue;
           const long long t = (g.plane / PX) * ((g.outer / CS) / RS);
           StencilCfg c;
-          if (t >= 32 && t <= 512 && try_cfg(g, true, CS, (int)t, nitems, &c) && c.px == PX &&
-              c.rs == RS)
+          if (t >= 32 && t <= 512 && try_cfg(g, true, CS, (int)t, nitems, &c, PX, RS))
             out[n++] = c;
         }
     } else {
