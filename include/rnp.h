@@ -70,12 +70,15 @@ typedef enum {
   RNP_ADVECT1D = 6     /* param: c                                         */
 } rnp_pde;
 
-typedef enum { RNP_FP64 = 0, RNP_MIXED = 1 } rnp_precision;
+typedef enum { RNP_FP64 = 0, RNP_MIXED = 1, RNP_MIXED_BF16 = 2 } rnp_precision;
 /* FP64: every step in double precision; F and G are bit-identical to a
  *       plain serial FP64 evaluation of the same formulas.
- * MIXED: F and G stencils in FP32 arithmetic, random features from BF16
- *       operands with FP32 accumulation, neighbour search screened in FP32
- *       and decided in FP64, ridge solve, correction and norm in FP64.   */
+ * MIXED: F and G stencils in FP32 arithmetic on a compensated (two-word)
+ *       FP32 state; random features and neighbour distances in FP32; ridge
+ *       solve, correction and norm in FP64.
+ * MIXED_BF16: as MIXED, but the random features use BF16 operands (weights
+ *       and scaled inputs rounded to BF16) with FP32 accumulation: batched
+ *       rows on the tensor cores (tcgen05), single queries on CUDA cores.  */
 
 typedef enum { RNP_EXEC_FUSED = 0, RNP_EXEC_PLAIN = 1 } rnp_exec;
 /* FUSED: one launch advances every active slice through all of its steps,
@@ -227,6 +230,11 @@ rnp_status rnp_reset(rnp_ctx* ctx);
 rnp_status rnp_get_pairs(rnp_ctx* ctx, long long* pairs);
 /* Unknowns per state. */
 long long rnp_dim(const rnp_problem* prob);
+/* Random features phi = ReLU(A s(u) + zeta) (Eq. HA) of R states with the
+ * context's scaling, weights and precision (MIXED_BF16: tensor cores).
+ * U : device [R][d] (unscaled), phi : device [R][M].  1 <= R <= B N.  Uses
+ * the context's fine-step buffer as scratch: not during rnp_iterate.      */
+rnp_status rnp_features(rnp_ctx* ctx, const double* U, int R, double* phi);
 /* Stencil launch configuration in use: which = 0 fine step, 1 coarse step.
  * out[0] cluster size, out[1] threads per CTA, out[2] x-points per thread
  * (0 for the FP64 kernel), out[3] rows per thread, out[4] 1 if chosen by

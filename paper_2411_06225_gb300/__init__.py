@@ -89,7 +89,7 @@ def problem(cfg: dict, precision: str = "fp64", exec: str = "fused", **kw) -> Pr
     p.corr = {"randnet": 0, "parareal": 1}[c.get("corr", "randnet")]
     p.scale_mode = {"minmax": 0, "none": 1}[c.get("scale", "minmax")]
     p.gscheme = {"euler": 0, "rk4": 1}[c.get("gscheme", "euler")]
-    p.precision = {"fp64": 0, "mixed": 1}[precision]
+    p.precision = {"fp64": 0, "mixed": 1, "mixed_bf16": 2}[precision]
     p.exec_ = {"fused": 0, "plain": 1}[exec]
     p.batch = c.get("batch", 1)
     p.cluster = c.get("cluster", 0)
@@ -142,6 +142,7 @@ def lib() -> C.CDLL:
         "rnp_dim": (C.c_longlong, [C.POINTER(Problem)]),
         "rnp_stencil_config": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int)]),
         "rnp_member_start": (C.c_int, [vp, C.c_int, dp]),
+        "rnp_features": (C.c_int, [vp, dp, C.c_int, dp]),
         "rnp_iterate": (C.c_int, [vp, C.POINTER(C.c_int)]),
         "rnp_member_status": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                         C.POINTER(C.c_int)]),
@@ -280,6 +281,13 @@ class Solver:
         return U
 
     # --- inspection ------------------------------------------------------
+    def features(self, U):
+        """Random features ReLU(A s(U) + zeta) of R states U [R, d]."""
+        R = U.shape[0]
+        phi = self._empty(R, self.M)
+        self._check(lib().rnp_features(self._ctx, _ptr(U, shape=(R, self.d)), R, _ptr(phi)))
+        return phi
+
     def weights(self):
         A = self._empty(self.M, self.d)
         z = self._empty(self.M)

@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "librnp.so")
-SOURCES = ["api.cu", "stencil.cu", "randnet.cu", "noalloc.cu"] + [
+SOURCES = ["api.cu", "stencil.cu", "randnet.cu", "noalloc.cu", "features_tc.cu"] + [
     f"stencil_{n}.cu" for n in ("burgers", "advect", "heat1", "heat2", "heat3",
                                 "diffreact", "bruss2", "bruss3", "swe")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -42,6 +42,9 @@ struct rnp_ctx {
   double *Sds = nullptr, *Yds = nullptr, *Phi = nullptr;
   double *A = nullptr, *zeta = nullptr;
   float *A32 = nullptr, *S32 = nullptr, *q32 = nullptr;  // mixed precision copies
+  __nv_bfloat16* Abf = nullptr;   // BF16 weights (MIXED_BF16)
+  float* tc_part = nullptr;       // split-K partials of the tensor-core feature GEMM
+  bool bf16 = false;
   double *sc = nullptr, *sr = nullptr, *scale_work = nullptr;
   double *feat_part = nullptr, *nn_part = nullptr, *dist = nullptr, *alpha = nullptr;
   int *idx = nullptr, *meff = nullptr, *flags = nullptr;  // flags: esc, fail, nonfinite
@@ -162,7 +165,8 @@ const char* validate(const rnp_problem* p) {
   if (p->scale_mode != RNP_SCALE_MINMAX && p->scale_mode != RNP_SCALE_NONE)
     return "unknown scale_mode";
   if (p->gscheme != RNP_G_EULER && p->gscheme != RNP_G_RK4) return "unknown gscheme";
-  if (p->precision != RNP_FP64 && p->precision != RNP_MIXED) return "unknown precision";
+  if (p->precision != RNP_FP64 && p->precision != RNP_MIXED && p->precision != RNP_MIXED_BF16)
+    return "unknown precision";
   if (p->exec != RNP_EXEC_FUSED && p->exec != RNP_EXEC_PLAIN) return "unknown exec";
   if (p->cluster < 0 || p->cluster > 16 || p->threads < 0 || p->threads > 512 ||
       p->threads % 32)
@@ -176,7 +180,7 @@ void destroy_buffers(rnp_ctx* c) {
                   c->Yds, c->Phi, c->A, c->zeta, c->sc, c->sr, c->scale_work, c->feat_part,
                   c->nn_part, c->dist, c->alpha, c->idx, c->meff, c->flags, c->dP, c->err,
                   c->plain_work, c->d_items, c->d_app, c->d_gate, c->A32, c->S32, c->q32,
-                  c->d_mask};
+                  c->d_mask, c->Abf, c->tc_part};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->h_items) cudaFreeHost(c->h_items);
@@ -230,7 +234,8 @@ Items affine(int n, long long sb, long long ss, long long db, long long ds, cons
 
 rnp_status ensure_weights(rnp_ctx* c) {
   if (c->weights_ready) return RNP_OK;
-  CK(launch_weights(c->p.seed, c->M, c->d, c->A, c->zeta, c->A32, nullptr, nullptr, c->st));
+  CK(launch_weights(c->p.seed, c->M, c->d, c->A, c->zeta, c->A32,
+                    reinterpret_cast<uint16_t*>(c->Abf), nullptr, c->st));
   c->weights_ready = true;
   return RNP_OK;
 }
@@ -266,8 +271,12 @@ rnp_status predict_core(rnp_ctx* c, const double* q, long long q_base, long long
     // mixed: FP32 query, FP32 features and FP32 distance screening
     CK(launch_scale_rows(c->g, q, src, nullptr, 1, c->sc, c->sr, nullptr, c->q32, qrows, c->B,
                          gate, c->st));
-    CK(launch_features32(c->A32, c->zeta, c->M, c->d, c->q32, qrows, c->B, phi_dst, prow,
-                         c->feat_part, gate, c->st));
+    if (c->bf16)
+      CK(launch_features_bf16(c->Abf, c->zeta, c->M, c->d, c->q32, qrows, c->B, phi_dst, prow,
+                              c->feat_part, gate, c->st));
+    else
+      CK(launch_features32(c->A32, c->zeta, c->M, c->d, c->q32, qrows, c->B, phi_dst, prow,
+                           c->feat_part, gate, c->st));
     CK(launch_nn_partial32(c->q32, c->S32, c->cap, c->d, c->dP, pm, c->B, c->nn_part, gate,
                            c->st));
   } else {
@@ -367,6 +376,27 @@ rnp_status solve_sweep(rnp_ctx* c, int i0) {
   return RNP_OK;
 }
 
+// Features of R dataset rows (scaled rows at S64/S32 + s_rows, written to
+// phi + phi_rows) in the context's precision: FP64, FP32, or BF16 operands on
+// the tensor cores.
+rnp_status batch_features(rnp_ctx* c, const double* S64, const float* S32, Rows s_rows, int R,
+                          double* phi, Rows phi_rows) {
+  if (R <= 0) return RNP_OK;
+  if (c->bf16 && c->M <= 128)
+    CK(launch_features_tc(c->Abf, c->zeta, c->M, c->d, S32, s_rows, R, phi, phi_rows,
+                          c->tc_part, c->flags + 3, c->st));
+  else if (c->bf16)
+    CK(launch_features_bf16(c->Abf, c->zeta, c->M, c->d, S32, s_rows, R, phi, phi_rows,
+                            c->feat_part, nullptr, c->st));
+  else if (c->fp32)
+    CK(launch_features32(c->A32, c->zeta, c->M, c->d, S32, s_rows, R, phi, phi_rows,
+                         c->feat_part, nullptr, c->st));
+  else
+    CK(launch_features64(c->A, c->zeta, c->M, c->d, S64, s_rows, R, phi, phi_rows,
+                         c->feat_part, nullptr, c->st));
+  return RNP_OK;
+}
+
 rnp_status read_flags(rnp_ctx* c, int* esc, int* failf, int* nonfinite) {
   CK(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
@@ -455,7 +485,8 @@ rnp_status rnp_create(const rnp_problem* prob, void* cuda_stream, rnp_ctx** out)
   c->coef = make_coef(*prob, c->g);
   c->B = prob->batch; c->N = prob->N; c->M = prob->M; c->m = prob->m;
   c->d = c->g.d;
-  c->fp32 = prob->precision == RNP_MIXED;
+  c->fp32 = prob->precision != RNP_FP64;
+  c->bf16 = prob->precision == RNP_MIXED_BF16;
   c->plain = prob->exec == RNP_EXEC_PLAIN;
   c->randnet = prob->corr == RNP_CORR_RANDNET;
   c->schemeG = prob->gscheme == RNP_G_RK4 ? SCHEME_RK4 : SCHEME_EULER;
@@ -501,6 +532,10 @@ rnp_status rnp_create(const rnp_problem* prob, void* cuda_stream, rnp_ctx** out)
   ok &= dalloc(&c->qbuf, (size_t)B * d) == cudaSuccess;
   ok &= dalloc(&c->phic, (size_t)B * N * M) == cudaSuccess;
   ok &= dalloc(&c->phiq, (size_t)B * M) == cudaSuccess;
+  if (c->bf16) {
+    ok &= dalloc(&c->Abf, (size_t)M * d) == cudaSuccess;
+    ok &= dalloc(&c->tc_part, features_tc_part_floats(c->feat_rows_cap, d)) == cudaSuccess;
+  }
   if (c->fp32) {
     ok &= dalloc(&c->A32, (size_t)M * d) == cudaSuccess;
     ok &= dalloc(&c->S32, (size_t)B * cap * d) == cudaSuccess;
@@ -658,6 +693,33 @@ rnp_status rnp_stencil_config(const rnp_ctx* c, int which, int* out) {
   return RNP_OK;
 }
 
+static rnp_status ensure_scaling_identity(rnp_ctx* c);
+
+rnp_status rnp_features(rnp_ctx* c, const double* U, int R, double* phi) {
+  if (!c) return RNP_EINVAL;
+  c->msg.clear();
+  if (!U || !phi || R < 1 || R > c->feat_rows_cap || R > c->itemcap)
+    return fail(c, RNP_EINVAL, "bad arguments (1 <= R <= %d)", std::min(c->feat_rows_cap, c->itemcap));
+  DevGuard gd(c->dev);
+  StreamJoin sj(c);
+  rnp_status s = ensure_weights(c);
+  if (s) return s;
+  if ((s = ensure_scaling_identity(c))) return s;
+  for (int r = 0; r < R; ++r) c->h_app[r] = 0;  // member 0's scaling
+  CK(cudaMemcpyAsync(c->d_app, c->h_app, sizeof(int) * R, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemsetAsync(c->flags, 0, sizeof(int) * 4, c->st));
+  Rows src{nullptr, 0, c->d}, dst{nullptr, 0, c->d}, prow{nullptr, 0, c->M};
+  double* S64 = c->Fv;                                // scratch rows
+  float* S32 = reinterpret_cast<float*>(c->Fv);
+  CK(launch_scale_rows(c->g, U, src, c->d_app, 1, c->sc, c->sr, c->fp32 ? nullptr : S64,
+                       c->fp32 ? S32 : nullptr, dst, R, nullptr, c->st));
+  if ((s = batch_features(c, S64, S32, dst, R, phi, prow))) return s;
+  CK(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (c->h_flags[3]) return fail(c, RNP_ETIMEOUT, "tensor-core feature GEMM wait timed out");
+  return RNP_OK;
+}
+
 rnp_status rnp_get_pairs(rnp_ctx* c, long long* pairs) {
   if (!c || !pairs) return RNP_EINVAL;
   for (int b = 0; b < c->B; ++b) pairs[b] = c->P[b];
@@ -685,6 +747,7 @@ rnp_status rnp_randnet_fit(rnp_ctx* c, const double* Uin, const double* Y, int P
   if (s) return s;
   if ((s = ensure_scaling_identity(c))) return s;
   // rows in chunks that fit the offset tables and the feature workspace
+  CK(cudaMemsetAsync(c->flags, 0, sizeof(int) * 4, c->st));
   const int chunk = std::min(c->itemcap, c->feat_rows_cap);
   const int R = c->B * P;
   long long* src = c->h_items;
@@ -709,14 +772,15 @@ rnp_status rnp_randnet_fit(rnp_ctx* c, const double* Uin, const double* Y, int P
                          c->fp32 ? c->S32 : nullptr, rdst, n, nullptr, c->st));
     CK(launch_copy_rows(Y, c->d_items, c->Yds, c->d_items + c->itemcap, c->d, n, c->st));
     Rows prow{c->d_items + 2 * c->itemcap, 0, 0};
-    if (c->fp32)
-      CK(launch_features32(c->A32, c->zeta, c->M, c->d, c->S32, rdst, n, c->Phi, prow,
-                           c->feat_part, nullptr, c->st));
-    else
-      CK(launch_features64(c->A, c->zeta, c->M, c->d, c->Sds, rdst, n, c->Phi, prow,
-                           c->feat_part, nullptr, c->st));
+    {
+      rnp_status fs = batch_features(c, c->Sds, c->S32, rdst, n, c->Phi, prow);
+      if (fs) return fs;
+    }
     CK(cudaStreamSynchronize(c->st));  // the staging tables are reused
   }
+  CK(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (c->h_flags[3]) return fail(c, RNP_ETIMEOUT, "tensor-core feature GEMM wait timed out");
   for (int b = 0; b < c->B; ++b) c->P[b] += P;
   return upload_P(c);
 }
@@ -894,12 +958,7 @@ rnp_status iterate_once(rnp_ctx* c, rnp_stats* st, int* n_active) {
     if (nfirst > 0) {  // first iteration: features of the k = 0 starts
       Rows srows{c->d_items + 2 * c->itemcap, 0, 0};
       Rows prow{c->d_items + 3 * c->itemcap, 0, 0};
-      if (c->fp32)
-        CK(launch_features32(c->A32, c->zeta, M, d, c->S32, srows, nfirst, c->Phi, prow,
-                             c->feat_part, nullptr, c->st));
-      else
-        CK(launch_features64(c->A, c->zeta, M, d, c->Sds, srows, nfirst, c->Phi, prow,
-                             c->feat_part, nullptr, c->st));
+      if ((s = batch_features(c, c->Sds, c->S32, srows, nfirst, c->Phi, prow))) return s;
     }
     if (nit > nfirst) {  // later iterations: the sweep already computed them
       AppendItems rest{c->d_app + nfirst, c->d_app + c->itemcap + nfirst,
@@ -926,8 +985,9 @@ rnp_status iterate_once(rnp_ctx* c, rnp_stats* st, int* n_active) {
   CK(cudaEventRecord(c->ev[3], c->st));
   CK(cudaMemcpyAsync(c->h_err, c->err, sizeof(unsigned long long) * B * (N + 1),
                      cudaMemcpyDeviceToHost, c->st));
-  CK(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
+  if (c->h_flags[3]) return fail(c, RNP_ETIMEOUT, "tensor-core feature GEMM wait timed out");
   CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
   st->t_fine_ms += ms;
   CK(cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]));

@@ -1,6 +1,7 @@
 // rnp_internal.h -- shared declarations of librnp's kernels and launchers.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -139,6 +140,20 @@ cudaError_t launch_features32(const float* A, const double* zeta, int M,
                               double* phi, Rows phi_rows, double* part,
                               const int* gate, cudaStream_t st);
 int features_chunks(long long d);
+
+// The same map with BF16 operands and FP32 accumulation: many rows on the
+// tensor cores (tcgen05, split-K; M <= 128, part holds
+// features_tc_part_floats(R, d) floats, err is set if a bounded wait gave
+// up) or single rows on CUDA cores (part as for launch_features64).
+size_t features_tc_part_floats(int R, long long d);
+cudaError_t launch_features_tc(const __nv_bfloat16* A, const double* zeta, int M,
+                               long long d, const float* S, Rows s_rows, int R,
+                               double* phi, Rows phi_rows, float* part, int* err,
+                               cudaStream_t st);
+cudaError_t launch_features_bf16(const __nv_bfloat16* A, const double* zeta, int M,
+                                 long long d, const float* S, Rows s_rows, int R,
+                                 double* phi, Rows phi_rows, double* part,
+                                 const int* gate, cudaStream_t st);
 
 // Squared distances of the scaled query q[b] to the P[b] stored rows of
 // member b (dataset rows at S + b * cap * d), partial over d-chunks.
