@@ -28,8 +28,12 @@ def dev(a):
 
 
 def bf16(a):
-    import torch
-    return torch.as_tensor(a, dtype=torch.float64).to(torch.bfloat16).double().numpy()
+    """Round-to-nearest-even to BF16 (8 significant bits) straight from the
+    FP64 value: one rounding (a conversion through FP32 rounds twice)."""
+    b = np.ascontiguousarray(a, np.float64).view(np.uint64)
+    lsb = (b >> np.uint64(45)) & np.uint64(1)
+    b = (b + np.uint64(0x00000FFFFFFFFFFF) + lsb) & ~np.uint64((1 << 45) - 1)
+    return b.view(np.float64)
 
 
 @pytest.mark.parametrize("nx,M,rows", [(64, 100, 64), (64, 100, 37), (128, 128, 64),
@@ -48,7 +52,7 @@ def test_feature_map_on_tensor_cores(R, nx, M, rows):
         A, z = A.cpu().numpy(), z.cpu().numpy()
     n = d // 2
     S = np.concatenate([(U[:, :n] - c[0, 0]) / r[0, 0], (U[:, n:] - c[0, 1]) / r[0, 1]], axis=1)
-    ref = np.maximum(bf16(S.astype(np.float32)) @ bf16(A).T + z, 0.0)
+    ref = np.maximum(bf16(S.astype(np.float32).astype(np.float64)) @ bf16(A).T + z, 0.0)
     exact = np.maximum(S @ A.T + z, 0.0)
     err = np.abs(phi - ref).max()
     assert err <= 1e-4 * np.abs(ref).max(), err
