@@ -8,8 +8,10 @@ of the 2D diffusion-reaction workload: 128 x 128 x 2 periodic grid
 (d = 32768), N = 64 slices on [0, 5], F = RK4 2000 steps/slice, G = forward
 Euler 8 steps/slice, M = 100 ReLU features, m = 4 neighbours, lambda = 1e-7,
 tol = 1e-6, initial state i.i.d. N(0,1) (seeded, synthetic).  The timed
-form is the mixed-precision fused path (FP32 stencils, FP64 correction,
-ridge and norm); the plain FP64 GPU form is timed beside it.
+form is the mixed-precision fused path (FP32 stencils on a compensated state,
+random features from BF16 operands with FP32 accumulation on the tensor
+cores, FP64 ridge, correction and norm); the plain FP64 GPU form is timed
+beside it.
 
 value = fine cell-updates per second over the whole job (sum over ranks of
 the fine RK4 unknown-steps the solves performed / max over ranks of the
@@ -306,7 +308,7 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": statistics.mean(tts), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16+f64" if args.precision == "mixed_bf16" else "f32+f64",
             "data": "synthetic",
             "config": {"workload": describe(cfg),
                        "precision": args.precision, "exec": "fused", "autotune": True,
@@ -350,7 +352,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed_bf16", choices=["mixed_bf16", "mixed", "fp64"])
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD,
