@@ -229,6 +229,22 @@ def run_gpu(args):
 
     for _ in range(args.warmup):
         solver.solve(u0)
+    if args.profile:
+        # the fine step and the batched feature map of the timed form, one each
+        U0 = solver.coarse_sweep(0, u0)
+        starts = U0[:, :N].contiguous()
+        torch.cuda.synchronize(dev)
+        torch.cuda.nvtx.range_push("rnp_fine")
+        solver.fine_batch(starts)
+        torch.cuda.synchronize(dev)
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.nvtx.range_push("rnp_features")
+        solver.features(starts[0])
+        torch.cuda.synchronize(dev)
+        torch.cuda.nvtx.range_pop()
+        solver.close()
+        print(json.dumps({"profile": "done", "precision": args.precision, "tiling": tiling}))
+        return 0
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -283,8 +299,12 @@ def run_gpu(args):
     extra = {}
     if rank == 0 and not args.skip_fp64:
         # plain FP64 GPU RandNet-Parareal (per-stage kernels, FP64 features)
-        for label, prec, ex in (("fp64_plain", "fp64", "plain"), ("fp64_fused", "fp64", "fused")):
-            with rnp.Solver(rnp.problem(cfg, precision=prec, exec=ex), stream=stream) as s2:
+        for label, prec, ex in (("fp64_plain", "fp64", "plain"), ("fp64_fused", "fp64", "fused"),
+                                ("mixed_bf16", "mixed_bf16", "fused")):
+            with rnp.Solver(rnp.problem(cfg, precision=prec, exec=ex, autotune=int(ex == "fused")),
+                            stream=stream) as s2:
+                if label == "mixed_bf16":
+                    s2.solve(u0)                   # warm-up (graph capture)
                 torch.cuda.synchronize(dev)
                 ev0.record(stream)
                 U2, st2 = s2.solve(u0)
@@ -293,7 +313,11 @@ def run_gpu(args):
                 extra[f"tts_{label}_ms"] = ev0.elapsed_time(ev1)
                 extra[f"K_{label}"] = st2["K"]
                 if label == "fp64_fused":
+                    Uf = U2.clone()
                     extra["mixed_vs_fp64_max_abs"] = float((U - U2).abs().max().item())
+                if label == "mixed_bf16":
+                    extra["mixed_bf16_vs_fp64_rel"] = float(((U2 - Uf).abs().max() /
+                                                              Uf.abs().max()).item())
                     extra["mixed_vs_fp64_rel"] = float(((U - U2).abs().max() /
                                                         U2.abs().max()).item())
 
@@ -352,7 +376,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed_bf16", choices=["mixed_bf16", "mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_bf16", "fp64"])
+    ap.add_argument("--profile", action="store_true",
+                    help="one solve, then one fine step and one batched feature map inside "
+                         "NVTX ranges 'rnp_fine' and 'rnp_features' (for ncu --nvtx)")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD,

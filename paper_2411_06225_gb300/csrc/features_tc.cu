@@ -30,7 +30,7 @@ namespace rnp {
 static const int kTcM = 128;      // rows per tile (tcgen05 M)
 static const int kTcN = 128;      // neurons per tile (tcgen05 N); M <= 128
 static const int kTcKB = 64;      // K elements per shared-memory block (128 B of BF16)
-static const int kTcChunk = 1024; // K elements per CTA (split-K chunk)
+static const int kTcChunk = 256;  // K elements per CTA (split-K chunk)
 static const long long kSpinLimit = 1LL << 20;
 
 int features_tc_chunks(long long d) { return (int)((d + kTcChunk - 1) / kTcChunk); }
