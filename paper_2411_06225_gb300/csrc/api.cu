@@ -216,7 +216,7 @@ rnp_status run_stencil(rnp_ctx* c, bool fine, const double* in, double* out, dou
                              c->plain_work, sx);
   else
     e = launch_stencil_fused(c->g, c->coef, c->fp32, scheme, steps, dt, in, out, out2, it,
-                             fine ? c->cfgF : c->cfgG, sx);
+                             fine ? c->cfgF : c->cfgG, sx, c->flags + 3);
   if (e != cudaSuccess)
     return fail(c, RNP_ECUDA, "stencil launch failed: %s", cudaGetErrorString(e));
   return RNP_OK;
@@ -397,9 +397,13 @@ rnp_status batch_features(rnp_ctx* c, const double* S64, const float* S32, Rows 
   return RNP_OK;
 }
 
+static const char* const kTimeoutMsg =
+    "a bounded device wait timed out (tensor-core feature GEMM or stencil halo exchange)";
+
 rnp_status read_flags(rnp_ctx* c, int* esc, int* failf, int* nonfinite) {
-  CK(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
+  if (c->h_flags[3]) return fail(c, RNP_ETIMEOUT, kTimeoutMsg);
   *esc = c->h_flags[0];
   *failf = c->h_flags[1];
   *nonfinite = c->h_flags[2];
@@ -431,7 +435,7 @@ rnp_status autotune_stencils(rnp_ctx* c) {
         CK(cudaEventRecord(c->ev[4], c->st));
         CK(launch_stencil_fused(c->g, c->coef, c->fp32, fine ? SCHEME_RK4 : c->schemeG, steps,
                                 fine ? c->dtF : c->dtG, c->U, c->Fv, nullptr, it, cands[k],
-                                c->st));
+                                c->st, c->flags + 3));
         CK(cudaEventRecord(c->ev[5], c->st));
         CK(cudaEventSynchronize(c->ev[5]));
         float ms = 0;
@@ -624,7 +628,13 @@ rnp_status rnp_fine_batch(rnp_ctx* c, const double* U_in, int n, double* U_out) 
   StreamJoin sj(c);
   Items it = affine(c->B * n, 0, c->d, 0, c->d, nullptr);
   if (!c->plain && c->B * n > c->B * c->N) return fail(c, RNP_EINVAL, "too many items");
-  return run_stencil(c, true, U_in, U_out, nullptr, it);
+  CK(cudaMemsetAsync(c->flags + 3, 0, sizeof(int), c->st));
+  rnp_status s = run_stencil(c, true, U_in, U_out, nullptr, it);
+  if (s) return s;
+  CK(cudaMemcpyAsync(c->h_flags + 3, c->flags + 3, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (c->h_flags[3]) return fail(c, RNP_ETIMEOUT, kTimeoutMsg);
+  return RNP_OK;
 }
 
 rnp_status rnp_get_weights(rnp_ctx* c, double* A, double* zeta) {
@@ -716,7 +726,7 @@ rnp_status rnp_features(rnp_ctx* c, const double* U, int R, double* phi) {
   if ((s = batch_features(c, S64, S32, dst, R, phi, prow))) return s;
   CK(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
-  if (c->h_flags[3]) return fail(c, RNP_ETIMEOUT, "tensor-core feature GEMM wait timed out");
+  if (c->h_flags[3]) return fail(c, RNP_ETIMEOUT, kTimeoutMsg);
   return RNP_OK;
 }
 
@@ -780,7 +790,7 @@ rnp_status rnp_randnet_fit(rnp_ctx* c, const double* Uin, const double* Y, int P
   }
   CK(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
-  if (c->h_flags[3]) return fail(c, RNP_ETIMEOUT, "tensor-core feature GEMM wait timed out");
+  if (c->h_flags[3]) return fail(c, RNP_ETIMEOUT, kTimeoutMsg);
   for (int b = 0; b < c->B; ++b) c->P[b] += P;
   return upload_P(c);
 }
@@ -878,8 +888,9 @@ rnp_status start_members(rnp_ctx* c, const std::vector<int>& want, const double*
   c->scaling_ready = true;
   if (c->randnet && (s = ensure_weights(c))) return s;
   CK(cudaEventRecord(c->ev[1], c->st));
-  CK(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
+  if (c->h_flags[3]) return fail(c, RNP_ETIMEOUT, kTimeoutMsg);
   if (c->h_flags[2]) return fail(c, RNP_ENONFINITE, "non-finite state in the k = 0 sweep");
   CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
   if (st) st->t_sweep_ms += ms;
@@ -987,7 +998,7 @@ rnp_status iterate_once(rnp_ctx* c, rnp_stats* st, int* n_active) {
                      cudaMemcpyDeviceToHost, c->st));
   CK(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
-  if (c->h_flags[3]) return fail(c, RNP_ETIMEOUT, "tensor-core feature GEMM wait timed out");
+  if (c->h_flags[3]) return fail(c, RNP_ETIMEOUT, kTimeoutMsg);
   CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
   st->t_fine_ms += ms;
   CK(cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]));

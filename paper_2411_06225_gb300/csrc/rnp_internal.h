@@ -95,7 +95,7 @@ cudaError_t launch_stencil_fused(const Geom& g, const Coef& c, bool fp32,
                                  int scheme, int steps, double dt,
                                  const double* in, double* out, double* out2,
                                  const Items& it, const StencilCfg& cfg,
-                                 cudaStream_t st);
+                                 cudaStream_t st, int* err = nullptr);
 
 // Plain stencil: one launch per Runge-Kutta stage over global memory.
 // work must hold 4 * n_items * d doubles.

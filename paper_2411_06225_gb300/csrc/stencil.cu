@@ -144,8 +144,12 @@ static int round_R(long long cells_per_thread) {
 
 static size_t smem_bytes(const Geom& g, bool fp32, int CS) {
   const long long ncell = (long long)(g.outer / CS) * g.plane;
-  // FP64 kernel: two stage buffers; mixed kernel: two buffers + the low words
-  return fp32 ? 3 * (size_t)g.ncomp * ncell * 4 : 2 * (size_t)g.ncomp * ncell * 8;
+  // FP64 kernel: two stage buffers; mixed kernel: two stage buffers and the
+  // low words, each with two ghost rows, then two mbarriers and the
+  // 16-byte halo target table
+  if (!fp32) return 2 * (size_t)g.ncomp * ncell * 8;
+  const size_t f = 3 * (size_t)g.ncomp * (ncell + 2 * g.plane) * 4;
+  return ((f + 15) & ~(size_t)15) + 32;
 }
 
 static bool launchable(FusedFn fn, int CS, int threads, size_t smem, int nitems) {
@@ -345,7 +349,7 @@ int list_stencil_cfgs(const Geom& g, bool fp32, int nitems, StencilCfg* out, int
 cudaError_t launch_stencil_fused(const Geom& g, const Coef& c, bool fp32, int scheme,
                                  int steps, double dt, const double* in, double* out,
                                  double* out2, const Items& it, const StencilCfg& cfg,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, int* err) {
   if (it.n <= 0 || steps <= 0) return cudaSuccess;
   // a mixed-precision context uses the FP64 kernel where no FP32 tile fits
   const bool use_mixed = fp32 && cfg.px > 0;
@@ -360,6 +364,7 @@ cudaError_t launch_stencil_fused(const Geom& g, const Coef& c, bool fp32, int sc
   P.coef = c;
   for (int i = 0; i < 12; ++i) P.kf[i] = (float)c.k[i];
   P.fdt = (float)P.dt; P.fh2 = (float)P.h2; P.fh6 = (float)P.h6;
+  P.err = err;
   cudaLaunchConfig_t lc = {};
   cudaLaunchAttribute at[1];
   lc.gridDim = dim3(cfg.cluster * it.n);

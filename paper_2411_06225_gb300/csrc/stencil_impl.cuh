@@ -148,6 +148,7 @@ struct FusedParams {
   Coef coef;
   float kf[12];      // coefficients rounded to FP32 (mixed kernel)
   float fdt, fh2, fh6;
+  int* err;          // set to 1 when a halo wait times out (mixed kernel)
 };
 
 template <int KP, typename T, bool EX, int R>
@@ -365,7 +366,9 @@ __global__ void k_stage_plain(const PlainParams P) {
 // ---------------------------------------------------------------------------
 // Mixed-precision fused kernel: FP32 arithmetic, compensated state.
 //
-// Same residency scheme as k_stencil_fused, with three differences:
+// Same residency as k_stencil_fused (one slice per cluster, split along the
+// outer axis, stage values double-buffered in shared memory), with these
+// differences:
 //  * the step state is an unevaluated sum u = uh + ul of two FP32 numbers;
 //    each step's increment is added with an error-free TwoSum (Knuth), so the
 //    state keeps ~48 bits over thousands of steps while every right-hand
@@ -373,7 +376,18 @@ __global__ void k_stage_plain(const PlainParams P) {
 //  * thread t owns PX adjacent x-points (vector shared-memory accesses) over
 //    RS consecutive outer rows: the outer-axis neighbours come from a rolling
 //    window of registers, only the x neighbours (and y in 3D) are loaded;
-//  * the four Runge-Kutta stages are unrolled at compile time.
+//  * the four Runge-Kutta stages are unrolled at compile time;
+//  * no CTA reads another CTA's stage buffer.  The threads that own a CTA's
+//    first or last outer row push that row's new stage values into the
+//    neighbouring CTA's halo rows (st.async into distributed shared memory,
+//    completing bytes on that CTA's mbarrier), so a stage ends with a CTA
+//    barrier instead of a cluster barrier.  Halos and mbarriers are
+//    double-buffered by stage parity.  The group owning the last row walks
+//    its rows downwards, so both edge rows are computed (and pushed) first
+//    in a stage and their halos are read a whole stage after they were sent.
+//    Every mbarrier wait is bounded: on timeout the kernel sets *err, all
+//    CTAs leave the step loop at the next stage boundary and meet at one
+//    final cluster barrier.
 // Requires nx % PX == 0 and (outer / cluster) % RS == 0.
 // ---------------------------------------------------------------------------
 template <int PX> struct VecT;
@@ -405,39 +419,126 @@ __device__ __forceinline__ void two_sum_acc(float& uh, float& ul, float x) {
   uh = h;
 }
 
+// --- distributed-shared-memory halo exchange ------------------------------
+static constexpr long long kHaloSpin = 1LL << 24;  // try_wait polls before a wait gives up
+
+__device__ __forceinline__ uint32_t cta_smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint32_t cluster_map_u32(uint32_t a, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+// PX FP32 values to another CTA's shared memory; completes PX*4 bytes on
+// that CTA's mbarrier.
+template <int PX>
+__device__ __forceinline__ void st_async_vec(uint32_t addr, const float* v, uint32_t mbar) {
+  if constexpr (PX == 2)
+    asm volatile(
+        "st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];"
+        ::"r"(addr), "f"(v[0]), "f"(v[1]), "r"(mbar) : "memory");
+  else if constexpr (PX == 4)
+    asm volatile(
+        "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];"
+        ::"r"(addr), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "r"(mbar) : "memory");
+  else
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f32 [%0], %1, [%2];"
+                 ::"r"(addr), "f"(v[0]), "r"(mbar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes)
+               : "memory");
+}
+// Bounded wait for the phase of the given parity; acquire at cluster scope
+// (the bytes were written by other CTAs of the cluster).
+__device__ __forceinline__ bool halo_wait(uint32_t mbar, uint32_t parity) {
+  for (long long it = 0; it < kHaloSpin; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n"
+        " mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Where a stage sends its edge rows: outer row 0 to the previous rank's
+// ghost row nloc, outer row nloc - 1 to the next rank's ghost row -1, both
+// in the buffer of the next stage's parity.  Addresses are 32-bit
+// shared-window addresses: the neighbours' windows (mapa) for a cluster of
+// several CTAs, this CTA's own window for a one-CTA cluster (periodic wrap
+// onto itself, written with plain shared stores).  The four targets are the
+// same for every thread of a CTA and sit in shared memory (tab: row-0
+// target, row-(nloc-1) target, previous / next rank's mbarrier 0), so the
+// register tile does not carry them.
+struct HaloOut {
+  bool on;               // false on the last stage of the launch
+  bool self;             // one-CTA cluster
+  bool first, last, edge;  // this thread owns outer row 0 / nloc - 1 / either
+  const uint4* tab;      // the CTA's target table
+  uint32_t boff;         // byte offset of buffer `parity` from buffer 0
+  uint32_t moff;         // byte offset of mbarrier `parity` from mbarrier 0
+};
+
+template <int PX>
+__device__ __forceinline__ void st_shared_vec(uint32_t addr, const float* v) {
+  if constexpr (PX == 2)
+    asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v[0]), "f"(v[1]) : "memory");
+  else if constexpr (PX == 4)
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v[0]), "f"(v[1]),
+                 "f"(v[2]), "f"(v[3]) : "memory");
+  else
+    asm volatile("st.shared.f32 [%0], %1;" ::"r"(addr), "f"(v[0]) : "memory");
+}
+
+// Sends PX values (element `elem` of the row, counted in floats from the
+// start of the buffer) of outer row 0 (to_prev) or nloc - 1.
+template <int PX>
+__device__ __forceinline__ void push_edge(const HaloOut& h, bool to_prev, uint32_t elem,
+                                          const float* v) {
+  const uint4 t = *h.tab;
+  const uint32_t a = (to_prev ? t.x : t.y) + h.boff + 4u * elem;
+  if (h.self) st_shared_vec<PX>(a, v);
+  else st_async_vec<PX>(a, v, (to_prev ? t.z : t.w) + h.moff);
+}
+
 template <int KP, int PX, int RS, int STAGE>
 __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* __restrict__ B,
-                                            float* __restrict__ Bn, const float* BP,
-                                            const float* BN, float* ulo,
+                                            float* __restrict__ Bn, float* ulo,
                                             float (&uh)[RS][KT<KP>::NC][PX],
                                             float (&acc)[RS][KT<KP>::NC][PX],
-                                            int ncell, int plane, int nloc, int o0,
+                                            int ncell, int plane, int nloc, int ofirst, int dir,
                                             int rowoff, int woff, int eoff, int yn_off, int ys_off,
-                                            bool euler) {
+                                            bool euler, const HaloOut& ho) {
   const float* kk = P.kf;
   const float dt = P.fdt, h2 = P.fh2, h6 = P.fh6;
   constexpr int NC = KT<KP>::NC, DIMS = KT<KP>::DIMS;
-  float prv[NC][PX], cur[NC][PX], nxt[NC][PX];
-  // rolling window along the outer axis (rows o0-1, o0, o0+1, ...)
+  // Only the shallow-water fluxes tell the two outer neighbours apart; the
+  // other right-hand sides take their sum.
+  constexpr bool kOrdered = KP == KP_SWE;
+  const int rstep = dir * plane;
+  // rolling window along the walking direction: `back` is the row behind
+  // the one being updated, `ahead` the row in front of it (ghost rows -1
+  // and nloc hold the neighbours' edge rows)
+  float back[NC][PX], cur[NC][PX], ahead[NC][PX];
 #pragma unroll
   for (int q = 0; q < NC; ++q) {
-    ld_vec<PX>(B + q * ncell + o0 * plane + rowoff, cur[q]);
-    if (DIMS >= 2) {
-      if (o0 > 0) ld_vec<PX>(B + q * ncell + (o0 - 1) * plane + rowoff, prv[q]);
-      else ld_vec<PX>(BP + q * ncell + (nloc - 1) * plane + rowoff, prv[q]);
-    }
+    const float* row = B + q * ncell + ofirst * plane + rowoff;
+    ld_vec<PX>(row, cur[q]);
+    if (DIMS >= 2) ld_vec<PX>(row - rstep, back[q]);
   }
 #pragma unroll
   for (int r = 0; r < RS; ++r) {
-    const int o = o0 + r;
-    const int cb = o * plane + rowoff;  // first cell of this tile row
+    const int o = ofirst + dir * r;
+    const int cb = o * plane + rowoff;    // first cell of this tile row
 #pragma unroll
-    for (int q = 0; q < NC; ++q) {
-      if (DIMS >= 2) {
-        if (o + 1 < nloc) ld_vec<PX>(B + q * ncell + cb + plane, nxt[q]);
-        else ld_vec<PX>(BN + q * ncell + rowoff, nxt[q]);
-      }
-    }
+    for (int q = 0; q < NC; ++q)
+      if (DIMS >= 2) ld_vec<PX>(B + q * ncell + cb + rstep, ahead[q]);
     float ew[NC], ee[NC];
     float yn[NC][PX], ys[NC][PX];
 #pragma unroll
@@ -461,11 +562,14 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
       float Cv[NC], Ev[NC], Wv[NC], Nv[NC], Sv[NC], Uv[NC], Dv[NC], k[NC];
 #pragma unroll
       for (int q = 0; q < NC; ++q) {
+        // outer neighbours o + 1 and o - 1
+        const float hi = kOrdered ? (dir > 0 ? ahead[q][p] : back[q][p]) : ahead[q][p];
+        const float lo = kOrdered ? (dir > 0 ? back[q][p] : ahead[q][p]) : back[q][p];
         Cv[q] = cur[q][p];
         Ev[q] = (p + 1 < PX) ? cur[q][p + 1] : ee[q];
         Wv[q] = (p > 0) ? cur[q][p - 1] : ew[q];
-        if (DIMS == 2) { Nv[q] = nxt[q][p]; Sv[q] = prv[q][p]; Uv[q] = Dv[q] = 0.f; }
-        else if (DIMS == 3) { Nv[q] = yn[q][p]; Sv[q] = ys[q][p]; Uv[q] = nxt[q][p]; Dv[q] = prv[q][p]; }
+        if (DIMS == 2) { Nv[q] = hi; Sv[q] = lo; Uv[q] = Dv[q] = 0.f; }
+        else if (DIMS == 3) { Nv[q] = yn[q][p]; Sv[q] = ys[q][p]; Uv[q] = hi; Dv[q] = lo; }
         else { Nv[q] = Sv[q] = Uv[q] = Dv[q] = 0.f; }
       }
       rhs_point<KP, float, false>(Cv, Ev, Wv, Nv, Sv, Uv, Dv, kk, k);
@@ -500,8 +604,14 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
     for (int q = 0; q < NC; ++q) {
       st_vec<PX>(Bn + q * ncell + cb, wout[q]);
       if (DIMS >= 2) {
+        // edge rows are visited first: row 0 (walking up) or nloc - 1 (down);
+        // a CTA with a single row group also sends its last row at r = RS - 1
+        if (r == 0 && ho.on && ho.edge)
+          push_edge<PX>(ho, ho.first, q * ncell + rowoff, wout[q]);
+        if (r == RS - 1 && ho.on && ho.first && ho.last)
+          push_edge<PX>(ho, false, q * ncell + rowoff, wout[q]);
 #pragma unroll
-        for (int p = 0; p < PX; ++p) { prv[q][p] = cur[q][p]; cur[q][p] = nxt[q][p]; }
+        for (int p = 0; p < PX; ++p) { back[q][p] = cur[q][p]; cur[q][p] = ahead[q][p]; }
       }
     }
   }
@@ -518,18 +628,22 @@ __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant_
   if (P.it.gate && !P.it.gate[item]) return; // uniform over the cluster
   const int plane = P.plane, nx = P.nx, ny = P.ny;
   const int nloc = P.outer / CS;
-  const int ncell = nloc * plane;
-  float* const buf0 = reinterpret_cast<float*>(smem_raw);
+  // shared memory: stage buffers 0/1 and the low words, each [NC][nloc + 2][plane]
+  // (outer rows -1 .. nloc; rows -1 and nloc of the stage buffers are the
+  // ghost rows), then two mbarriers
+  const int ncell = (nloc + 2) * plane;
+  float* const buf0 = reinterpret_cast<float*>(smem_raw) + plane;   // row 0 of buffer 0
   float* const buf1 = buf0 + NC * ncell;
   float* const ulo = buf1 + NC * ncell;
-  const float *rp0 = buf0, *rp1 = buf1, *rn0 = buf0, *rn1 = buf1;
-  if (CS > 1) {
-    cg::cluster_group cl = cg::this_cluster();
-    const int rp = (rank + CS - 1) % CS, rn = (rank + 1) % CS;
-    rp0 = cl.map_shared_rank(buf0, rp);
-    rp1 = cl.map_shared_rank(buf1, rp);
-    rn0 = cl.map_shared_rank(buf0, rn);
-    rn1 = cl.map_shared_rank(buf1, rn);
+  uint64_t* const mbar = reinterpret_cast<uint64_t*>(
+      smem_raw + ((((size_t)3 * NC * ncell) * 4 + 15) & ~(size_t)15));
+  const bool remote = DIMS >= 2 && CS > 1;
+  const uint32_t sbase = cta_smem_u32(smem_raw);
+  const uint32_t mb0 = cta_smem_u32(mbar);
+  if (remote && threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb0) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb0 + 8) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // tile of this thread: PX x-points at inner offset rowoff, rows o0 .. o0+RS-1
   const int tiles = plane / PX;
@@ -544,8 +658,38 @@ __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant_
   const int ys_off = (DIMS == 3 ? ((yrow == 0 ? ny - 1 : yrow - 1) * nx) : 0) + x0;
   // first cells of the tiles west and east of this one (periodic in x)
   const int woff = yrow * nx + (xw + 1 - PX), eoff = yrow * nx + xe;
+  const bool first = o0 == 0, last = o0 + RS == nloc;
+  const bool edge = DIMS >= 2 && (first || last);
+  // the group owning the last row (unless it also owns the first) walks
+  // downwards; register tile row r is outer row ofirst + dir * r
+  const int dir = (last && !first) ? -1 : 1;
+  const int ofirst = dir > 0 ? o0 : o0 + RS - 1;
 
-  const long long base = (long long)rank * ncell;
+  // halo targets: my first row is the previous rank's ghost row nloc, my
+  // last row the next rank's ghost row -1 (buffer 0; +boff for buffer 1)
+  uint4* const tab = reinterpret_cast<uint4*>(mbar + 2);
+  if (threadIdx.x == 0) {
+    uint32_t rb_prev = sbase, rb_next = sbase;
+    if (remote) {
+      rb_prev = cluster_map_u32(sbase, (rank + CS - 1) % CS);
+      rb_next = cluster_map_u32(sbase, (rank + 1) % CS);
+    }
+    *tab = make_uint4(rb_prev + (uint32_t)((nloc + 1) * plane) * 4u, rb_next,
+                      rb_prev + (mb0 - sbase), rb_next + (mb0 - sbase));
+  }
+  auto halo_out = [&](int par, bool on) {
+    HaloOut h;
+    h.on = on;
+    h.self = !remote;
+    h.first = first; h.last = last; h.edge = edge;
+    h.tab = tab;
+    h.boff = (uint32_t)(par * NC * ncell) * 4u;
+    h.moff = 8u * par;
+    return h;
+  };
+  const uint32_t tx_bytes = (uint32_t)(2 * NC * plane * 4);
+
+  const long long base = (long long)rank * nloc * plane;
   const double* in = P.in + item_off(P.it.src_off, P.it.src_base, P.it.src_stride, item) + base;
   float uh[RS][NC][PX], acc[RS][NC][PX];
 #pragma unroll
@@ -554,42 +698,83 @@ __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant_
     for (int q = 0; q < NC; ++q)
 #pragma unroll
       for (int p = 0; p < PX; ++p) {
-        const int cell = (o0 + r) * plane + rowoff + p;
-        const double v = in[q * P.n + cell];
+        const int o = ofirst + dir * r;
+        const double v = in[q * P.n + o * plane + rowoff + p];
         const float h = (float)v;
         uh[r][q][p] = h;
         acc[r][q][p] = 0.f;
-        buf0[q * ncell + cell] = h;
-        ulo[q * ncell + cell] = (float)(v - (double)h);
+        buf0[q * ncell + o * plane + rowoff + p] = h;
+        ulo[q * ncell + o * plane + rowoff + p] = (float)(v - (double)h);
       }
+  // every CTA's mbarriers and target table are initialised before anyone
+  // pushes
   if (CS > 1) cg::this_cluster().sync(); else __syncthreads();
-
-  const bool rk4 = P.scheme == SCHEME_RK4;
-  for (int step = 0; step < P.steps; ++step) {
-    if (rk4) {
-      mixed_stage<KP, PX, RS, 0>(P, buf0, buf1, rp0, rn0, ulo, uh, acc, ncell, plane, nloc, o0,
-                                 rowoff, woff, eoff, yn_off, ys_off, false);
-      if (CS > 1) cg::this_cluster().sync(); else __syncthreads();
-      mixed_stage<KP, PX, RS, 1>(P, buf1, buf0, rp1, rn1, ulo, uh, acc, ncell, plane, nloc, o0,
-                                 rowoff, woff, eoff, yn_off, ys_off, false);
-      if (CS > 1) cg::this_cluster().sync(); else __syncthreads();
-      mixed_stage<KP, PX, RS, 2>(P, buf0, buf1, rp0, rn0, ulo, uh, acc, ncell, plane, nloc, o0,
-                                 rowoff, woff, eoff, yn_off, ys_off, false);
-      if (CS > 1) cg::this_cluster().sync(); else __syncthreads();
-      mixed_stage<KP, PX, RS, 3>(P, buf1, buf0, rp1, rn1, ulo, uh, acc, ncell, plane, nloc, o0,
-                                 rowoff, woff, eoff, yn_off, ys_off, false);
-      if (CS > 1) cg::this_cluster().sync(); else __syncthreads();
-    } else {
-      // forward Euler: buffers alternate every step
-      if ((step & 1) == 0)
-        mixed_stage<KP, PX, RS, 0>(P, buf0, buf1, rp0, rn0, ulo, uh, acc, ncell, plane, nloc, o0,
-                                 rowoff, woff, eoff, yn_off, ys_off, true);
-      else
-        mixed_stage<KP, PX, RS, 0>(P, buf1, buf0, rp1, rn1, ulo, uh, acc, ncell, plane, nloc, o0,
-                                 rowoff, woff, eoff, yn_off, ys_off, true);
-      if (CS > 1) cg::this_cluster().sync(); else __syncthreads();
+  // stage 0's halo: the initial edge rows
+  if (DIMS >= 2) {
+    const HaloOut h0 = halo_out(0, true);
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      // outer rows 0 and nloc - 1 sit in register rows 0 / RS - 1 or, walking
+      // downwards, RS - 1 / 0
+      float v0[PX], v1[PX];
+#pragma unroll
+      for (int p = 0; p < PX; ++p) {
+        v0[p] = dir > 0 ? uh[0][q][p] : uh[RS - 1][q][p];
+        v1[p] = dir > 0 ? uh[RS - 1][q][p] : uh[0][q][p];
+      }
+      if (first) push_edge<PX>(h0, true, q * ncell + rowoff, v0);
+      if (last) push_edge<PX>(h0, false, q * ncell + rowoff, v1);
     }
   }
+  __syncthreads();
+
+  // Stage s reads buffer s & 1 (with its ghost rows) and writes buffer
+  // (s + 1) & 1 and the neighbours' ghost rows of that buffer.  Before
+  // reading ghost rows pushed by other CTAs the edge threads wait for the
+  // phase of mbarrier s & 1 whose parity is (s >> 1) & 1.
+  bool bad = false;
+  auto stage_begin = [&](int s) {
+    if (!remote) return;
+    if (threadIdx.x == 0) mbar_expect(mb0 + 8u * (s & 1), tx_bytes);
+    if (edge && !halo_wait(mb0 + 8u * (s & 1), (uint32_t)((s >> 1) & 1))) {
+      bad = true;
+      if (P.err) atomicExch(P.err, 1);
+    }
+  };
+#define RNP_MIXED_STAGE(STG, BIN, BOUT, PAR, ON, EUL)                                          \
+  mixed_stage<KP, PX, RS, STG>(P, BIN, BOUT, ulo, uh, acc, ncell, plane, nloc, ofirst, dir,   \
+                               rowoff, woff, eoff, yn_off, ys_off, EUL, halo_out((PAR) ^ 1, ON))
+
+  const bool rk4 = P.scheme == SCHEME_RK4;
+  const int nst = rk4 ? 4 * P.steps : P.steps;
+  for (int step = 0; step < P.steps; ++step) {
+    if (rk4) {
+      const int s0 = 4 * step;
+      stage_begin(s0);
+      RNP_MIXED_STAGE(0, buf0, buf1, 0, true, false);
+      if (__syncthreads_or(bad)) break;
+      stage_begin(s0 + 1);
+      RNP_MIXED_STAGE(1, buf1, buf0, 1, true, false);
+      if (__syncthreads_or(bad)) break;
+      stage_begin(s0 + 2);
+      RNP_MIXED_STAGE(2, buf0, buf1, 0, true, false);
+      if (__syncthreads_or(bad)) break;
+      stage_begin(s0 + 3);
+      RNP_MIXED_STAGE(3, buf1, buf0, 1, s0 + 4 < nst, false);
+      if (__syncthreads_or(bad)) break;
+    } else {
+      // forward Euler: buffers alternate every step
+      stage_begin(step);
+      if ((step & 1) == 0)
+        RNP_MIXED_STAGE(0, buf0, buf1, 0, step + 1 < nst, true);
+      else
+        RNP_MIXED_STAGE(0, buf1, buf0, 1, step + 1 < nst, true);
+      if (__syncthreads_or(bad)) break;
+    }
+  }
+#undef RNP_MIXED_STAGE
+  // no CTA leaves while a neighbour may still address its shared memory
+  if (CS > 1) cg::this_cluster().sync();
   double* out = P.out + item_off(P.it.dst_off, P.it.dst_base, P.it.dst_stride, item) + base;
   double* out2 = P.out2 ? P.out2 + item_off(P.it.dst2_off, P.it.dst2_base, P.it.dst2_stride, item) + base
                         : nullptr;
@@ -599,10 +784,10 @@ __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant_
     for (int q = 0; q < NC; ++q)
 #pragma unroll
       for (int p = 0; p < PX; ++p) {
-        const int cell = (o0 + r) * plane + rowoff + p;
-        const double v = (double)uh[r][q][p] + (double)ulo[q * ncell + cell];
-        out[q * P.n + cell] = v;
-        if (out2) out2[q * P.n + cell] = v;
+        const int o = ofirst + dir * r;
+        const double v = (double)uh[r][q][p] + (double)ulo[q * ncell + o * plane + rowoff + p];
+        out[q * P.n + o * plane + rowoff + p] = v;
+        if (out2) out2[q * P.n + o * plane + rowoff + p] = v;
       }
 }
 
