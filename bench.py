@@ -222,7 +222,14 @@ def run_gpu(args):
     u0_h = torch.as_tensor(W.initial_condition(cfg)).pin_memory()
     u0 = u0_h.to(dev)
     stream = torch.cuda.current_stream(dev)
-    prob = rnp.problem(cfg, precision=args.precision, exec="fused", autotune=1)
+    if args.tile:
+        # a fixed stencil tiling (cluster, threads), e.g. to profile one
+        # configuration: the autotuner's pick can differ under a profiler
+        c_, t_ = (int(x) for x in args.tile.split(","))
+        prob = rnp.problem(cfg, precision=args.precision, exec="fused", autotune=0,
+                           cluster=c_, threads=t_)
+    else:
+        prob = rnp.problem(cfg, precision=args.precision, exec="fused", autotune=1)
     solver = rnp.Solver(prob, stream=stream)
     tiling = {"fine": solver.stencil_config("fine"), "coarse": solver.stencil_config("coarse")}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
@@ -240,6 +247,11 @@ def run_gpu(args):
         torch.cuda.nvtx.range_pop()
         torch.cuda.nvtx.range_push("rnp_features")
         solver.features(starts[0])
+        torch.cuda.synchronize(dev)
+        torch.cuda.nvtx.range_pop()
+        solver.reset()
+        torch.cuda.nvtx.range_push("rnp_solve")
+        solver.solve(u0)
         torch.cuda.synchronize(dev)
         torch.cuda.nvtx.range_pop()
         solver.close()
@@ -378,13 +390,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_bf16", "fp64"])
     ap.add_argument("--profile", action="store_true",
-                    help="one solve, then one fine step and one batched feature map inside "
-                         "NVTX ranges 'rnp_fine' and 'rnp_features' (for ncu --nvtx)")
+                    help="one solve, then one fine step, one batched feature map and one "
+                         "more solve inside NVTX ranges 'rnp_fine', 'rnp_features' and "
+                         "'rnp_solve' (for ncu --nvtx)")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=["diffreact2d", "burgers1d", "bruss2d", "bruss3d"])
     ap.add_argument("--max-iters", type=int, default=0)
+    ap.add_argument("--tile", default="",
+                    help="fixed stencil tiling 'cluster,threads' instead of the autotuner's")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

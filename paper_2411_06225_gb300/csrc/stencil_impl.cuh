@@ -370,7 +370,7 @@ __global__ void k_stage_plain(const PlainParams P) {
 // outer axis, stage values double-buffered in shared memory), with these
 // differences:
 //  * the step state is an unevaluated sum u = uh + ul of two FP32 numbers;
-//    each step's increment is added with an error-free TwoSum (Knuth), so the
+//    each step's increment is added with Fast2Sum (Dekker), so the
 //    state keeps ~48 bits over thousands of steps while every right-hand
 //    side is evaluated in FP32 (uh in registers, ul in shared memory);
 //  * thread t owns PX adjacent x-points (vector shared-memory accesses) over
@@ -408,11 +408,13 @@ __device__ __forceinline__ void st_vec(float* p, const float* v) {
   else { *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]); }
 }
 
-// (uh, ul) += x without rounding error in the sum (TwoSum, then renormalise).
+// (uh, ul) += x, keeping the rounding error of the sum: Dekker's Fast2Sum
+// (exact when |uh| >= |x|, i.e. whenever the step increment is smaller than
+// the state; where the state crosses zero the error term is approximate, to
+// within an ulp of the increment), then renormalise.
 __device__ __forceinline__ void two_sum_acc(float& uh, float& ul, float x) {
   const float s = __fadd_rn(uh, x);
-  const float bb = __fsub_rn(s, uh);
-  const float err = __fadd_rn(__fsub_rn(uh, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+  const float err = __fsub_rn(x, __fsub_rn(s, uh));
   const float l = __fadd_rn(ul, err);
   const float h = __fadd_rn(s, l);
   ul = __fsub_rn(l, __fsub_rn(h, s));
@@ -726,17 +728,20 @@ __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant_
       if (last) push_edge<PX>(h0, false, q * ncell + rowoff, v1);
     }
   }
-  __syncthreads();
 
   // Stage s reads buffer s & 1 (with its ghost rows) and writes buffer
-  // (s + 1) & 1 and the neighbours' ghost rows of that buffer.  Before
-  // reading ghost rows pushed by other CTAs the edge threads wait for the
-  // phase of mbarrier s & 1 whose parity is (s >> 1) & 1.
+  // (s + 1) & 1 and the neighbours' ghost rows of that buffer.  Before the
+  // CTA barrier that opens stage s, thread 0 arms mbarrier s & 1 for the
+  // ghost-row bytes and waits for its phase (parity (s >> 1) & 1) with
+  // cluster-scope acquire; the barrier then passes the ghost rows on to the
+  // CTA's other threads.
+  const bool rk4 = P.scheme == SCHEME_RK4;
+  const int nst = rk4 ? 4 * P.steps : P.steps;
   bool bad = false;
-  auto stage_begin = [&](int s) {
-    if (!remote) return;
-    if (threadIdx.x == 0) mbar_expect(mb0 + 8u * (s & 1), tx_bytes);
-    if (edge && !halo_wait(mb0 + 8u * (s & 1), (uint32_t)((s >> 1) & 1))) {
+  auto halo_ready = [&](int s) {
+    if (!remote || threadIdx.x != 0 || s >= nst) return;
+    mbar_expect(mb0 + 8u * (s & 1), tx_bytes);
+    if (!halo_wait(mb0 + 8u * (s & 1), (uint32_t)((s >> 1) & 1))) {
       bad = true;
       if (P.err) atomicExch(P.err, 1);
     }
@@ -745,31 +750,32 @@ __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant_
   mixed_stage<KP, PX, RS, STG>(P, BIN, BOUT, ulo, uh, acc, ncell, plane, nloc, ofirst, dir,   \
                                rowoff, woff, eoff, yn_off, ys_off, EUL, halo_out((PAR) ^ 1, ON))
 
-  const bool rk4 = P.scheme == SCHEME_RK4;
-  const int nst = rk4 ? 4 * P.steps : P.steps;
-  for (int step = 0; step < P.steps; ++step) {
-    if (rk4) {
-      const int s0 = 4 * step;
-      stage_begin(s0);
-      RNP_MIXED_STAGE(0, buf0, buf1, 0, true, false);
-      if (__syncthreads_or(bad)) break;
-      stage_begin(s0 + 1);
-      RNP_MIXED_STAGE(1, buf1, buf0, 1, true, false);
-      if (__syncthreads_or(bad)) break;
-      stage_begin(s0 + 2);
-      RNP_MIXED_STAGE(2, buf0, buf1, 0, true, false);
-      if (__syncthreads_or(bad)) break;
-      stage_begin(s0 + 3);
-      RNP_MIXED_STAGE(3, buf1, buf0, 1, s0 + 4 < nst, false);
-      if (__syncthreads_or(bad)) break;
-    } else {
-      // forward Euler: buffers alternate every step
-      stage_begin(step);
-      if ((step & 1) == 0)
-        RNP_MIXED_STAGE(0, buf0, buf1, 0, step + 1 < nst, true);
-      else
-        RNP_MIXED_STAGE(0, buf1, buf0, 1, step + 1 < nst, true);
-      if (__syncthreads_or(bad)) break;
+  halo_ready(0);
+  if (!__syncthreads_or(bad)) {
+    for (int step = 0; step < P.steps; ++step) {
+      if (rk4) {
+        const int s0 = 4 * step;
+        RNP_MIXED_STAGE(0, buf0, buf1, 0, true, false);
+        halo_ready(s0 + 1);
+        if (__syncthreads_or(bad)) break;
+        RNP_MIXED_STAGE(1, buf1, buf0, 1, true, false);
+        halo_ready(s0 + 2);
+        if (__syncthreads_or(bad)) break;
+        RNP_MIXED_STAGE(2, buf0, buf1, 0, true, false);
+        halo_ready(s0 + 3);
+        if (__syncthreads_or(bad)) break;
+        RNP_MIXED_STAGE(3, buf1, buf0, 1, s0 + 4 < nst, false);
+        halo_ready(s0 + 4);
+        if (__syncthreads_or(bad)) break;
+      } else {
+        // forward Euler: buffers alternate every step
+        if ((step & 1) == 0)
+          RNP_MIXED_STAGE(0, buf0, buf1, 0, step + 1 < nst, true);
+        else
+          RNP_MIXED_STAGE(0, buf1, buf0, 1, step + 1 < nst, true);
+        halo_ready(step + 1);
+        if (__syncthreads_or(bad)) break;
+      }
     }
   }
 #undef RNP_MIXED_STAGE
