@@ -118,17 +118,24 @@ static FusedFn fused_fn(int kp, bool fp32, int R) {
   return nullptr;
 }
 
-static FusedFn mixed_fn(int kp, int PX, int RS) {
+// x-neighbours by warp shuffles when an x-row of PX-point tiles spans a
+// power-of-two number of lanes that divides the warp
+static bool x_shuffles(const Geom& g, int PX) {
+  const int w = g.nx / PX;
+  return w >= 1 && w <= 32 && (32 % w) == 0;
+}
+
+static FusedFn mixed_fn(int kp, int PX, int RS, bool XS) {
   switch (kp) {
-    case KP_BURGERS: return mixed_fn_burgers(PX, RS);
-    case KP_ADVECT: return mixed_fn_advect(PX, RS);
-    case KP_HEAT1: return mixed_fn_heat1(PX, RS);
-    case KP_HEAT2: return mixed_fn_heat2(PX, RS);
-    case KP_HEAT3: return mixed_fn_heat3(PX, RS);
-    case KP_DIFFREACT: return mixed_fn_diffreact(PX, RS);
-    case KP_BRUSS2: return mixed_fn_bruss2(PX, RS);
-    case KP_BRUSS3: return mixed_fn_bruss3(PX, RS);
-    case KP_SWE: return mixed_fn_swe(PX, RS);
+    case KP_BURGERS: return mixed_fn_burgers(PX, RS, XS);
+    case KP_ADVECT: return mixed_fn_advect(PX, RS, XS);
+    case KP_HEAT1: return mixed_fn_heat1(PX, RS, XS);
+    case KP_HEAT2: return mixed_fn_heat2(PX, RS, XS);
+    case KP_HEAT3: return mixed_fn_heat3(PX, RS, XS);
+    case KP_DIFFREACT: return mixed_fn_diffreact(PX, RS, XS);
+    case KP_BRUSS2: return mixed_fn_bruss2(PX, RS, XS);
+    case KP_BRUSS3: return mixed_fn_bruss3(PX, RS, XS);
+    case KP_SWE: return mixed_fn_swe(PX, RS, XS);
   }
   return nullptr;
 }
@@ -145,11 +152,11 @@ static int round_R(long long cells_per_thread) {
 static size_t smem_bytes(const Geom& g, bool fp32, int CS) {
   const long long ncell = (long long)(g.outer / CS) * g.plane;
   // FP64 kernel: two stage buffers; mixed kernel: two stage buffers and the
-  // low words, each with two ghost rows, then two mbarriers and the
-  // 16-byte halo target table
+  // low words, each with two ghost rows, then two mbarriers, the 16-byte
+  // halo target table and two abort flags
   if (!fp32) return 2 * (size_t)g.ncomp * ncell * 8;
   const size_t f = 3 * (size_t)g.ncomp * (ncell + 2 * g.plane) * 4;
-  return ((f + 15) & ~(size_t)15) + 32;
+  return ((f + 15) & ~(size_t)15) + 48;
 }
 
 static bool launchable(FusedFn fn, int CS, int threads, size_t smem, int nitems) {
@@ -223,7 +230,7 @@ static bool try_cfg(const Geom& g, bool fp32, int CS, int threads, int nitems,
         const long long t = tiles * (nloc / RS);
         if (t > 512 || t < 1) continue;
         if (threads > 0 && t != threads) continue;
-        FusedFn fn = mixed_fn(g.kp, PX, RS);
+        FusedFn fn = mixed_fn(g.kp, PX, RS, x_shuffles(g, PX));
         if (!fn || !launchable(fn, CS, (int)t, smem, nitems)) continue;
         out->cluster = CS;
         out->threads = (int)t;
@@ -353,7 +360,8 @@ cudaError_t launch_stencil_fused(const Geom& g, const Coef& c, bool fp32, int sc
   if (it.n <= 0 || steps <= 0) return cudaSuccess;
   // a mixed-precision context uses the FP64 kernel where no FP32 tile fits
   const bool use_mixed = fp32 && cfg.px > 0;
-  FusedFn fn = use_mixed ? mixed_fn(g.kp, cfg.px, cfg.rs) : fused_fn(g.kp, false, cfg.R);
+  FusedFn fn = use_mixed ? mixed_fn(g.kp, cfg.px, cfg.rs, x_shuffles(g, cfg.px))
+                         : fused_fn(g.kp, false, cfg.R);
   if (!fn) return cudaErrorInvalidValue;
   FusedParams P;
   P.in = in; P.out = out; P.out2 = out2;

@@ -509,14 +509,15 @@ __device__ __forceinline__ void push_edge(const HaloOut& h, bool to_prev, uint32
   else st_async_vec<PX>(a, v, (to_prev ? t.z : t.w) + h.moff);
 }
 
-template <int KP, int PX, int RS, int STAGE>
+template <int KP, int PX, int RS, int STAGE, bool XS>
 __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* __restrict__ B,
                                             float* __restrict__ Bn, float* ulo,
                                             float (&uh)[RS][KT<KP>::NC][PX],
                                             float (&acc)[RS][KT<KP>::NC][PX],
                                             int ncell, int plane, int nloc, int ofirst, int dir,
                                             int rowoff, int woff, int eoff, int yn_off, int ys_off,
-                                            bool euler, const HaloOut& ho) {
+                                            bool euler, const HaloOut& ho, unsigned xmask,
+                                            int xw, int xwest, int xeast) {
   const float* kk = P.kf;
   const float dt = P.fdt, h2 = P.fh2, h6 = P.fh6;
   constexpr int NC = KT<KP>::NC, DIMS = KT<KP>::DIMS;
@@ -546,13 +547,20 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
       const float* Bq = B + q * ncell + o * plane;
-      // x neighbours: aligned vector loads of the adjacent tiles (lanes read
-      // consecutive vectors, so there is no bank conflict); keep the edge
-      float vw[PX], ve[PX];
-      ld_vec<PX>(Bq + woff, vw);
-      ld_vec<PX>(Bq + eoff, ve);
-      ew[q] = vw[PX - 1];
-      ee[q] = ve[0];
+      if constexpr (XS) {
+        // x neighbours from the adjacent lanes: an x-row spans xw lanes, so
+        // a width-xw shuffle wraps periodically in x
+        ew[q] = __shfl_sync(xmask, cur[q][PX - 1], xwest, xw);
+        ee[q] = __shfl_sync(xmask, cur[q][0], xeast, xw);
+      } else {
+        // x neighbours: aligned vector loads of the adjacent tiles (lanes
+        // read consecutive vectors, so there is no bank conflict); keep the edge
+        float vw[PX], ve[PX];
+        ld_vec<PX>(Bq + woff, vw);
+        ld_vec<PX>(Bq + eoff, ve);
+        ew[q] = vw[PX - 1];
+        ee[q] = ve[0];
+      }
       if (DIMS == 3) {
         ld_vec<PX>(Bq + yn_off, yn[q]);
         ld_vec<PX>(Bq + ys_off, ys[q]);
@@ -619,7 +627,7 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
   }
 }
 
-template <int KP, int PX, int RS>
+template <int KP, int PX, int RS, bool XS>
 __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant__ FusedParams P) {
   constexpr int NC = KT<KP>::NC, DIMS = KT<KP>::DIMS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -666,11 +674,18 @@ __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant_
   // downwards; register tile row r is outer row ofirst + dir * r
   const int dir = (last && !first) ? -1 : 1;
   const int ofirst = dir > 0 ? o0 : o0 + RS - 1;
+  // x-neighbour shuffles: an x-row is xsw = nx / PX consecutive lanes
+  const int xsw = nx / PX;
+  const int xl = (int)(threadIdx.x & 31) & (xsw - 1);
+  const int xwest = (xl + xsw - 1) & (xsw - 1), xeast = (xl + 1) & (xsw - 1);
+  const unsigned xmask = blockDim.x >= 32 ? 0xffffffffu : ((1u << blockDim.x) - 1u);
 
   // halo targets: my first row is the previous rank's ghost row nloc, my
   // last row the next rank's ghost row -1 (buffer 0; +boff for buffer 1)
   uint4* const tab = reinterpret_cast<uint4*>(mbar + 2);
+  volatile int* const abort_flag = reinterpret_cast<volatile int*>(tab + 1);  // [2]
   if (threadIdx.x == 0) {
+    abort_flag[0] = abort_flag[1] = 0;
     uint32_t rb_prev = sbase, rb_next = sbase;
     if (remote) {
       rb_prev = cluster_map_u32(sbase, (rank + CS - 1) % CS);
@@ -730,52 +745,58 @@ __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant_
   }
 
   // Stage s reads buffer s & 1 (with its ghost rows) and writes buffer
-  // (s + 1) & 1 and the neighbours' ghost rows of that buffer.  Before the
-  // CTA barrier that opens stage s, thread 0 arms mbarrier s & 1 for the
-  // ghost-row bytes and waits for its phase (parity (s >> 1) & 1) with
-  // cluster-scope acquire; the barrier then passes the ghost rows on to the
-  // CTA's other threads.
+  // (s + 1) & 1 and the neighbours' ghost rows of that buffer.  At the start
+  // of stage s thread 0 arms mbarrier s & 1 for the ghost-row bytes, and the
+  // threads that read ghost rows (those owning an edge row) wait for its
+  // phase, parity (s >> 1) & 1, with cluster-scope acquire; the other warps
+  // start computing at once.
   const bool rk4 = P.scheme == SCHEME_RK4;
   const int nst = rk4 ? 4 * P.steps : P.steps;
-  bool bad = false;
-  auto halo_ready = [&](int s) {
-    if (!remote || threadIdx.x != 0 || s >= nst) return;
-    mbar_expect(mb0 + 8u * (s & 1), tx_bytes);
-    if (!halo_wait(mb0 + 8u * (s & 1), (uint32_t)((s >> 1) & 1))) {
-      bad = true;
+  auto stage_begin = [&](int s) {
+    if (!remote) return;
+    if (threadIdx.x == 0) mbar_expect(mb0 + 8u * (s & 1), tx_bytes);
+    if (edge && !halo_wait(mb0 + 8u * (s & 1), (uint32_t)((s >> 1) & 1))) {
+      abort_flag[s & 1] = 1;
       if (P.err) atomicExch(P.err, 1);
     }
   };
+  // CTA barrier closing stage s; true when a wait of stage s gave up.  The
+  // flag of stage s is written before this barrier and read after it; the
+  // next write to it (stage s + 2) comes after the barrier of stage s + 1,
+  // so every thread reads the same value and leaves at the same stage.
+  auto stage_end = [&](int s) {
+    __syncthreads();
+    return abort_flag[s & 1] != 0;
+  };
 #define RNP_MIXED_STAGE(STG, BIN, BOUT, PAR, ON, EUL)                                          \
-  mixed_stage<KP, PX, RS, STG>(P, BIN, BOUT, ulo, uh, acc, ncell, plane, nloc, ofirst, dir,   \
-                               rowoff, woff, eoff, yn_off, ys_off, EUL, halo_out((PAR) ^ 1, ON))
+  mixed_stage<KP, PX, RS, STG, XS>(P, BIN, BOUT, ulo, uh, acc, ncell, plane, nloc, ofirst,    \
+                                   dir, rowoff, woff, eoff, yn_off, ys_off, EUL,             \
+                                   halo_out((PAR) ^ 1, ON), xmask, xsw, xwest, xeast)
 
-  halo_ready(0);
-  if (!__syncthreads_or(bad)) {
-    for (int step = 0; step < P.steps; ++step) {
-      if (rk4) {
-        const int s0 = 4 * step;
-        RNP_MIXED_STAGE(0, buf0, buf1, 0, true, false);
-        halo_ready(s0 + 1);
-        if (__syncthreads_or(bad)) break;
-        RNP_MIXED_STAGE(1, buf1, buf0, 1, true, false);
-        halo_ready(s0 + 2);
-        if (__syncthreads_or(bad)) break;
-        RNP_MIXED_STAGE(2, buf0, buf1, 0, true, false);
-        halo_ready(s0 + 3);
-        if (__syncthreads_or(bad)) break;
-        RNP_MIXED_STAGE(3, buf1, buf0, 1, s0 + 4 < nst, false);
-        halo_ready(s0 + 4);
-        if (__syncthreads_or(bad)) break;
-      } else {
-        // forward Euler: buffers alternate every step
-        if ((step & 1) == 0)
-          RNP_MIXED_STAGE(0, buf0, buf1, 0, step + 1 < nst, true);
-        else
-          RNP_MIXED_STAGE(0, buf1, buf0, 1, step + 1 < nst, true);
-        halo_ready(step + 1);
-        if (__syncthreads_or(bad)) break;
-      }
+  __syncthreads();
+  for (int step = 0; step < P.steps; ++step) {
+    if (rk4) {
+      const int s0 = 4 * step;
+      stage_begin(s0);
+      RNP_MIXED_STAGE(0, buf0, buf1, 0, true, false);
+      if (stage_end(s0)) break;
+      stage_begin(s0 + 1);
+      RNP_MIXED_STAGE(1, buf1, buf0, 1, true, false);
+      if (stage_end(s0 + 1)) break;
+      stage_begin(s0 + 2);
+      RNP_MIXED_STAGE(2, buf0, buf1, 0, true, false);
+      if (stage_end(s0 + 2)) break;
+      stage_begin(s0 + 3);
+      RNP_MIXED_STAGE(3, buf1, buf0, 1, s0 + 4 < nst, false);
+      if (stage_end(s0 + 3)) break;
+    } else {
+      // forward Euler: buffers alternate every step
+      stage_begin(step);
+      if ((step & 1) == 0)
+        RNP_MIXED_STAGE(0, buf0, buf1, 0, step + 1 < nst, true);
+      else
+        RNP_MIXED_STAGE(0, buf1, buf0, 1, step + 1 < nst, true);
+      if (stage_end(step)) break;
     }
   }
 #undef RNP_MIXED_STAGE
@@ -812,22 +833,39 @@ inline FusedFn fused_for_R(int R) {
   }
 }
 
-template <int KP, int PX>
+// Register tiles of more than kMaxTileValues state values per thread spill
+// beyond use and are not instantiated (the host picker never asks for them).
+static constexpr int kMaxTileValues = 40;
+
+template <int KP, int PX, int RS, bool XS>
+inline FusedFn mixed_if_fits() {
+  if constexpr (RS * KT<KP>::NC * PX <= kMaxTileValues) return k_stencil_mixed<KP, PX, RS, XS>;
+  else return nullptr;
+}
+
+template <int KP, int PX, bool XS>
 inline FusedFn mixed_for_RS(int RS) {
   switch (RS) {
-    case 1: return k_stencil_mixed<KP, PX, 1>;
-    case 2: return k_stencil_mixed<KP, PX, 2>;
-    case 4: return k_stencil_mixed<KP, PX, 4>;
-    case 5: return k_stencil_mixed<KP, PX, 5>;
-    case 8: return k_stencil_mixed<KP, PX, 8>;
+    case 1: return mixed_if_fits<KP, PX, 1, XS>();
+    case 2: return mixed_if_fits<KP, PX, 2, XS>();
+    case 4: return mixed_if_fits<KP, PX, 4, XS>();
+    case 5: return mixed_if_fits<KP, PX, 5, XS>();
+    case 8: return mixed_if_fits<KP, PX, 8, XS>();
     default: return nullptr;
   }
+}
+
+template <int KP>
+inline FusedFn mixed_for(int PX, int RS, bool XS) {
+  if (PX == 2) return XS ? mixed_for_RS<KP, 2, true>(RS) : mixed_for_RS<KP, 2, false>(RS);
+  if (PX == 4) return XS ? mixed_for_RS<KP, 4, true>(RS) : mixed_for_RS<KP, 4, false>(RS);
+  return nullptr;
 }
 
 // Per-PDE entry points, defined in stencil_<pde>.cu.
 #define RNP_STENCIL_DECL(NAME)                 \
   FusedFn fused_fn_##NAME(bool fp32, int R);   \
-  FusedFn mixed_fn_##NAME(int PX, int RS);     \
+  FusedFn mixed_fn_##NAME(int PX, int RS, bool XS); \
   PlainFn plain_fn_##NAME();
 RNP_STENCIL_DECL(burgers)
 RNP_STENCIL_DECL(advect)
@@ -844,9 +882,7 @@ RNP_STENCIL_DECL(swe)
   FusedFn fused_fn_##NAME(bool fp32, int R) {                                        \
     return fp32 ? fused_for_R<KPV, float, false>(R) : fused_for_R<KPV, double, true>(R); \
   }                                                                                  \
-  FusedFn mixed_fn_##NAME(int PX, int RS) {                                         \
-    return PX == 2 ? mixed_for_RS<KPV, 2>(RS) : PX == 4 ? mixed_for_RS<KPV, 4>(RS) : nullptr; \
-  }                                                                                  \
+  FusedFn mixed_fn_##NAME(int PX, int RS, bool XS) { return mixed_for<KPV>(PX, RS, XS); } \
   PlainFn plain_fn_##NAME() { return k_stage_plain<KPV>; }
 
 }  // namespace rnp
