@@ -202,14 +202,12 @@ static const int kFeatFW = 16;
 int features_chunks(long long d) { return (int)((d + kFeatCH - 1) / kFeatCH); }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_feat_partial(const T* A, int M, long long d,
-                                                      const T* S, Rows rows, int R,
-                                                      double* part, int nch,
-                                                      const int* gate) {
-  __shared__ T sS[kFeatTR][kFeatCH];
-  const int ch = blockIdx.x;
-  const int r0 = blockIdx.y * kFeatTR;
-  const int w0 = blockIdx.z * kFeatFW;
+__device__ __forceinline__ void feat_partial_body(T (&sS)[kFeatTR][kFeatCH], const T* A, int M,
+                                                  long long d, const T* S, Rows rows, int R,
+                                                  double* part, int nch, const int* gate,
+                                                  int ch, int ry, int wz) {
+  const int r0 = ry * kFeatTR;
+  const int w0 = wz * kFeatFW;
   const long long j0 = (long long)ch * kFeatCH;
   const int len = (int)((d - j0) < kFeatCH ? (d - j0) : kFeatCH);
   bool any = false;
@@ -248,6 +246,16 @@ __global__ void __launch_bounds__(256) k_feat_partial(const T* A, int M, long lo
         if (r0 + r < R) part[((long long)(r0 + r) * M + w) * nch + ch] = (double)acc[r];
     }
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_feat_partial(const T* A, int M, long long d,
+                                                      const T* S, Rows rows, int R,
+                                                      double* part, int nch,
+                                                      const int* gate) {
+  __shared__ T sS[kFeatTR][kFeatCH];
+  feat_partial_body<T>(sS, A, M, d, S, rows, R, part, nch, gate, blockIdx.x, blockIdx.y,
+                       blockIdx.z);
 }
 
 __global__ void k_feat_finish(const double* part, int nch, int R, int M, const double* zeta,
@@ -308,20 +316,18 @@ static long long nn_chunk_len(long long d) {
 int nn_chunks(long long d) { return (int)((d + nn_chunk_len(d) - 1) / nn_chunk_len(d)); }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_nn_partial(const T* q, const T* S, long long cap,
-                                                    long long d, long long chl,
-                                                    const int* P, double* part, int nch,
-                                                    const int* gate) {
-  const int b = blockIdx.z;
+__device__ __forceinline__ void nn_partial_body(const T* q, const T* S, long long cap,
+                                                long long d, long long chl, const int* P,
+                                                double* part, int nch, const int* gate,
+                                                int ch, int by, int gy, int b) {
   if (gate && !gate[b]) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int Pb = P[b];
-  const int ch = blockIdx.x;
   const long long j0 = (long long)ch * chl;
   const long long j1 = (j0 + chl) < d ? j0 + chl : d;
   const T* qb = q + (long long)b * d;
   // grid-stride over the stored rows: the grid does not depend on P
-  for (int p = blockIdx.y * kNnRows + warp; p < Pb; p += gridDim.y * kNnRows) {
+  for (int p = by * kNnRows + warp; p < Pb; p += gy * kNnRows) {
     const T* Sp = S + ((long long)b * cap + p) * d;
     T acc0 = T(0), acc1 = T(0);
     long long j = j0 + lane;
@@ -340,6 +346,36 @@ __global__ void __launch_bounds__(256) k_nn_partial(const T* q, const T* S, long
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) part[((long long)b * cap + p) * nch + ch] = (double)acc;
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_nn_partial(const T* q, const T* S, long long cap,
+                                                    long long d, long long chl,
+                                                    const int* P, double* part, int nch,
+                                                    const int* gate) {
+  nn_partial_body<T>(q, S, cap, d, chl, P, part, nch, gate, blockIdx.x, blockIdx.y, gridDim.y,
+                     blockIdx.z);
+}
+
+// One launch for both halves of a RandNet query: blocks [0, nfb) compute the
+// feature partials of the B query rows (grid nch_f x nry x nwz, flattened),
+// the rest the distance partials (grid nch_n x gy x B, flattened).
+template <typename T>
+__global__ void __launch_bounds__(256) k_query_partials(
+    const T* A, int M, long long d, const T* q, Rows qrows, int R, double* fpart, int fnch,
+    int nry, int nfb, const T* S, long long cap, long long chl, const int* P, double* npart,
+    int nnch, int gy, const int* gate) {
+  __shared__ T sS[kFeatTR][kFeatCH];
+  int bid = blockIdx.x;
+  if (bid < nfb) {
+    const int ch = bid % fnch, rest = bid / fnch;
+    feat_partial_body<T>(sS, A, M, d, q, qrows, R, fpart, fnch, gate, ch, rest % nry,
+                         rest / nry);
+    return;
+  }
+  bid -= nfb;
+  const int ch = bid % nnch, rest = bid / nnch;
+  nn_partial_body<T>(q, S, cap, d, chl, P, npart, nnch, gate, ch, rest % gy, gy, rest / gy);
 }
 
 template <typename T>
@@ -370,63 +406,119 @@ cudaError_t launch_nn_partial32(const float* q, const float* S, long long cap, l
   return launch_nn_t<float>(q, S, cap, d, P, Pmax, B, part, gate, st);
 }
 
+template <typename T>
+static cudaError_t launch_query_t(const T* A, int M, long long d, const T* q, int B,
+                                  double* fpart, const T* S, long long cap, const int* P,
+                                  int Pmax, double* npart, const int* gate, cudaStream_t st) {
+  if (B <= 0) return cudaSuccess;
+  const int fnch = features_chunks(d);
+  const int nry = (B + kFeatTR - 1) / kFeatTR, nwz = (M + kFeatFW - 1) / kFeatFW;
+  const int nfb = fnch * nry * nwz;
+  const int nnch = nn_chunks(d);
+  int gy = (Pmax + kNnRows - 1) / kNnRows;
+  if (gy > 32) gy = 32;
+  if (Pmax <= 0) gy = 0;
+  const long long nblocks = (long long)nfb + (long long)nnch * gy * B;
+  count_launches(1);
+  k_query_partials<T><<<(unsigned)nblocks, 256, 0, st>>>(
+      A, M, d, q, Rows{nullptr, 0, d}, B, fpart, fnch, nry, nfb, S, cap, nn_chunk_len(d), P,
+      npart, nnch, gy > 0 ? gy : 1, gate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_query64(const double* A, int M, long long d, const double* q, int B,
+                           double* fpart, const double* S, long long cap, const int* P,
+                           int Pmax, double* npart, const int* gate, cudaStream_t st) {
+  return launch_query_t<double>(A, M, d, q, B, fpart, S, cap, P, Pmax, npart, gate, st);
+}
+
+cudaError_t launch_query32(const float* A, int M, long long d, const float* q, int B,
+                           double* fpart, const float* S, long long cap, const int* P,
+                           int Pmax, double* npart, const int* gate, cudaStream_t st) {
+  return launch_query_t<float>(A, M, d, q, B, fpart, S, cap, P, Pmax, npart, gate, st);
+}
+
 // ---------------------------------------------------------------------------
 // Top-m selection + dual ridge solve, one CTA per member.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool lex_less(double a, int ia, double b, int ib) {
+// Distances are sums of squares (>= 0 or NaN), so their bit patterns order
+// like the values and a NaN orders after +inf: the selection compares 64-bit
+// integer keys (ties -> lower index).
+__device__ __forceinline__ bool key_less(unsigned long long a, int ia, unsigned long long b,
+                                         int ib) {
   return a < b || (a == b && ia < ib);
 }
 
 __global__ void __launch_bounds__(256) k_topm_ridge(const double* part, int nch,
                                                     const double* Phi, long long cap, int M,
-                                                    const double* phiq, long long phiq_bstride,
-                                                    const int* Pn, int m, double lambda,
-                                                    double* dist, double* alpha, int* idx,
-                                                    int* meff, int* esc_count, int* fail,
-                                                    const int* gate) {
+                                                    double* phiq, long long phiq_bstride,
+                                                    const double* fpart, int fnch,
+                                                    const double* zeta, const int* Pn, int m,
+                                                    double lambda, double* dist, double* alpha,
+                                                    int* idx, int* meff, int* esc_count,
+                                                    int* fail, const int* gate) {
   const int b = blockIdx.x;
   if (gate && !gate[b]) return;
   const int P = Pn[b];
   const int me = m < P ? m : P;
   __shared__ int sel[RNP_MAX_M];
-  __shared__ double wd[32];
+  __shared__ unsigned long long wk[32];
   __shared__ int wi[32];
   __shared__ double Kraw[RNP_MAX_M * RNP_MAX_M];
   __shared__ double L[RNP_MAX_M * RNP_MAX_M];
-  __shared__ double rhs[RNP_MAX_M], y[RNP_MAX_M], x[RNP_MAX_M];
+  __shared__ double rhs[RNP_MAX_M], y[RNP_MAX_M], x[RNP_MAX_M], linv[RNP_MAX_M];
+  double* pq = phiq + (long long)b * phiq_bstride;
+  // query features (when their partials are given): the chunk partials in
+  // chunk order, + zeta, ReLU -- the arithmetic of k_feat_finish
+  if (fpart) {
+    for (int w = threadIdx.x; w < M; w += blockDim.x) {
+      const double* fp = fpart + ((long long)b * M + w) * fnch;
+      double acc = 0.0;
+      for (int k = 0; k < fnch; ++k) acc = acc + fp[k];
+      const double v = acc + zeta[w];
+      pq[w] = v > 0.0 ? v : 0.0;
+    }
+  }
+  // distances: four interleaved partial sums over the chunks, then combined
   double* db = dist + (long long)b * cap;
   for (int p = threadIdx.x; p < P; p += blockDim.x) {
     const double* pp = part + ((long long)b * cap + p) * nch;
-    double acc = 0.0;
-    for (int k = 0; k < nch; ++k) acc = acc + pp[k];
-    db[p] = acc;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int k = 0;
+    for (; k + 3 < nch; k += 4) {
+      a0 = a0 + pp[k];
+      a1 = a1 + pp[k + 1];
+      a2 = a2 + pp[k + 2];
+      a3 = a3 + pp[k + 3];
+    }
+    for (; k < nch; ++k) a0 = a0 + pp[k];
+    db[p] = (a0 + a1) + (a2 + a3);
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int l = 0; l < me; ++l) {
-    double bd = 1.0 / 0.0;
+    unsigned long long bk = ~0ULL;
     int bi = 0x7fffffff;
     for (int p = threadIdx.x; p < P; p += blockDim.x) {
       bool taken = false;
       for (int k = 0; k < l; ++k) taken |= (sel[k] == p);
       if (taken) continue;
-      double v = db[p];
-      if (v != v) v = 1.0 / 0.0;  // a NaN distance ranks last, never unselected
-      if (lex_less(v, p, bd, bi)) { bd = v; bi = p; }
+      const unsigned long long v = (unsigned long long)__double_as_longlong(db[p]);
+      if (key_less(v, p, bk, bi)) { bk = v; bi = p; }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const double od = __shfl_xor_sync(0xffffffffu, bd, o);
+      const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
       const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (lex_less(od, oi, bd, bi)) { bd = od; bi = oi; }
+      if (key_less(ok, oi, bk, bi)) { bk = ok; bi = oi; }
     }
-    if (lane == 0) { wd[warp] = bd; wi[warp] = bi; }
+    if (lane == 0) { wk[warp] = bk; wi[warp] = bi; }
     __syncthreads();
     if (threadIdx.x == 0) {
-      double xd = wd[0];
+      unsigned long long xk = wk[0];
       int xi = wi[0];
       for (int k = 1; k < nw; ++k)
-        if (lex_less(wd[k], wi[k], xd, xi)) { xd = wd[k]; xi = wi[k]; }
+        if (key_less(wk[k], wi[k], xk, xi)) { xk = wk[k]; xi = wi[k]; }
       sel[l] = xi;
     }
     __syncthreads();
@@ -434,7 +526,6 @@ __global__ void __launch_bounds__(256) k_topm_ridge(const double* part, int nch,
   // Gram entries K[i][j] = sum_w X_i,w X_j,w (i >= j) and rhs_i = X_i . phi_q:
   // one warp per entry, lanes stride w, fixed butterfly reduction.
   const double* X = Phi + (long long)b * cap * M;
-  const double* pq = phiq + (long long)b * phiq_bstride;
   const int nK = me * (me + 1) / 2;
   for (int t = warp; t < nK + me; t += nw) {
     const double *xa, *xb;
@@ -464,6 +555,8 @@ __global__ void __launch_bounds__(256) k_topm_ridge(const double* part, int nch,
   meff[b] = me;
   for (int l = 0; l < me; ++l) idx[b * RNP_MAX_M + l] = sel[l];
   if (me == 0) return;
+  // Cholesky of K + lambda I with one division per column (the reciprocal
+  // of the pivot multiplies the column and both triangular solves)
   double lam = lambda;
   int ok = 0, tries = 0;
   for (tries = 0; tries <= 4 && !ok; ++tries) {
@@ -473,11 +566,13 @@ __global__ void __launch_bounds__(256) k_topm_ridge(const double* part, int nch,
       for (int k = 0; k < j; ++k) s = __dsub_rn(s, __dmul_rn(L[j * RNP_MAX_M + k], L[j * RNP_MAX_M + k]));
       if (!(s > 0.0)) { ok = 0; break; }
       const double ljj = __dsqrt_rn(s);
+      const double inv = __ddiv_rn(1.0, ljj);
       L[j * RNP_MAX_M + j] = ljj;
+      linv[j] = inv;
       for (int i = j + 1; i < me; ++i) {
         double t = Kraw[i * RNP_MAX_M + j];
         for (int k = 0; k < j; ++k) t = __dsub_rn(t, __dmul_rn(L[i * RNP_MAX_M + k], L[j * RNP_MAX_M + k]));
-        L[i * RNP_MAX_M + j] = __ddiv_rn(t, ljj);
+        L[i * RNP_MAX_M + j] = __dmul_rn(t, inv);
       }
     }
     if (!ok) lam = __dmul_rn(lam, 10.0);
@@ -491,44 +586,46 @@ __global__ void __launch_bounds__(256) k_topm_ridge(const double* part, int nch,
   for (int i = 0; i < me; ++i) {
     double t = rhs[i];
     for (int k = 0; k < i; ++k) t = __dsub_rn(t, __dmul_rn(L[i * RNP_MAX_M + k], y[k]));
-    y[i] = __ddiv_rn(t, L[i * RNP_MAX_M + i]);
+    y[i] = __dmul_rn(t, linv[i]);
   }
   for (int i = me - 1; i >= 0; --i) {
     double t = y[i];
     for (int k = i + 1; k < me; ++k) t = __dsub_rn(t, __dmul_rn(L[k * RNP_MAX_M + i], x[k]));
-    x[i] = __ddiv_rn(t, L[i * RNP_MAX_M + i]);
+    x[i] = __dmul_rn(t, linv[i]);
   }
   for (int l = 0; l < me; ++l) alpha[b * RNP_MAX_M + l] = x[l];
 }
 
 cudaError_t launch_topm_ridge(const double* part, int nch, const double* Phi, long long cap,
-                              int M, const double* phiq, long long phiq_bstride, const int* P,
-                              int Pmax, int B, int m, double lambda, double* dist,
-                              double* alpha, int* idx, int* meff, int* esc_count, int* fail,
-                              const int* gate, cudaStream_t st) {
+                              int M, double* phiq, long long phiq_bstride, const double* fpart,
+                              int fnch, const double* zeta, const int* P, int Pmax, int B,
+                              int m, double lambda, double* dist, double* alpha, int* idx,
+                              int* meff, int* esc_count, int* fail, const int* gate,
+                              cudaStream_t st) {
   (void)Pmax;
   count_launches(1);
-  k_topm_ridge<<<B, 256, 0, st>>>(part, nch, Phi, cap, M, phiq, phiq_bstride, P, m, lambda,
-                                  dist, alpha, idx, meff, esc_count, fail, gate);
+  k_topm_ridge<<<B, 256, 0, st>>>(part, nch, Phi, cap, M, phiq, phiq_bstride, fpart, fnch, zeta,
+                                  P, m, lambda, dist, alpha, idx, meff, esc_count, fail, gate);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
 // Update of Eq. 3 with the max-norm of Eq. 5 fused in.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void block_max_to(unsigned long long* dst, double v) {
-  __shared__ double red[32];
-  for (int o = 16; o > 0; o >>= 1) {
-    const double w = __shfl_xor_sync(0xffffffffu, v, o);
-    v = w > v ? w : v;
-  }
+// Block maximum of non-negative doubles (or NaN) given as their bit
+// patterns, which order like the values; one atomicMax per block.
+__device__ __forceinline__ void block_max_to(unsigned long long* dst, unsigned long long v) {
+  __shared__ unsigned long long red[32];
+  const unsigned hi = __reduce_max_sync(0xffffffffu, (unsigned)(v >> 32));
+  const unsigned lo = __reduce_max_sync(0xffffffffu, (unsigned)(v >> 32) == hi ? (unsigned)v : 0u);
+  v = ((unsigned long long)hi << 32) | lo;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) red[warp] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double x = red[0];
+    unsigned long long x = red[0];
     for (int k = 1; k < (int)(blockDim.x >> 5); ++k) x = red[k] > x ? red[k] : x;
-    atomicMax(dst, (unsigned long long)__double_as_longlong(x));
+    atomicMax(dst, x);
   }
 }
 
@@ -551,7 +648,7 @@ __global__ void __launch_bounds__(256) k_update(const double* g, long long g_bst
   __syncthreads();
   const double* gb = g ? g + (long long)b * g_bstride : nullptr;
   double* ob = out + (long long)b * out_bstride;
-  double emax = 0.0;
+  unsigned long long emax = 0ULL;  // bits of a non-negative double
   bool bad = false;
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < d;
        j += (long long)gridDim.x * blockDim.x) {
@@ -559,7 +656,7 @@ __global__ void __launch_bounds__(256) k_update(const double* g, long long g_bst
     for (int l = 0; l < me; ++l) acc = __dadd_rn(acc, __dmul_rn(a[l], Yl[l][j]));
     const double v = gb ? __dadd_rn(gb[j], acc) : acc;
     if (err) {
-      const double e = fabs(v - ob[j]);
+      const unsigned long long e = (unsigned long long)__double_as_longlong(fabs(v - ob[j]));
       emax = e > emax ? e : emax;
     }
     bad |= !isfinite(v);
@@ -581,13 +678,13 @@ __global__ void __launch_bounds__(256) k_update_para(const double* g, long long 
   const double* gb = g + (long long)b * g_bstride;
   const double* yb = Yv + (long long)b * yv_bstride;
   double* ob = out + (long long)b * out_bstride;
-  double emax = 0.0;
+  unsigned long long emax = 0ULL;  // bits of a non-negative double
   bool bad = false;
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < d;
        j += (long long)gridDim.x * blockDim.x) {
     const double v = __dadd_rn(gb[j], yb[j]);
     if (err) {
-      const double e = fabs(v - ob[j]);
+      const unsigned long long e = (unsigned long long)__double_as_longlong(fabs(v - ob[j]));
       emax = e > emax ? e : emax;
     }
     bad |= !isfinite(v);

@@ -165,13 +165,25 @@ cudaError_t launch_nn_partial32(const float* q, const float* S, long long cap,
                                 double* part, const int* gate, cudaStream_t st);
 int nn_chunks(long long d);
 
-// Per member: finish distances, select the m nearest (ties -> lower index),
-// build the dual ridge system from the stored features and phi_q, solve by
-// Cholesky (lambda x10 on a non-positive pivot, at most 4 times) and write
-// alpha[b*RNP_MAX_M + l], idx[b*RNP_MAX_M + l], meff[b].
+// Both partial sums of a RandNet query in one launch: the feature partials
+// of the B query rows q + b * d (fpart, as launch_features64's part) and the
+// distance partials to the stored rows (npart, as launch_nn_partial's part).
+cudaError_t launch_query64(const double* A, int M, long long d, const double* q, int B,
+                           double* fpart, const double* S, long long cap, const int* P,
+                           int Pmax, double* npart, const int* gate, cudaStream_t st);
+cudaError_t launch_query32(const float* A, int M, long long d, const float* q, int B,
+                           double* fpart, const float* S, long long cap, const int* P,
+                           int Pmax, double* npart, const int* gate, cudaStream_t st);
+
+// Per member: (if fpart != null) finish the query features phi_q from their
+// chunk partials into phiq[b]; finish distances, select the m nearest (ties
+// -> lower index), build the dual ridge system from the stored features and
+// phi_q, solve by Cholesky (lambda x10 on a non-positive pivot, at most 4
+// times) and write alpha[b*RNP_MAX_M + l], idx[b*RNP_MAX_M + l], meff[b].
 cudaError_t launch_topm_ridge(const double* part, int nch, const double* Phi,
-                              long long cap, int M, const double* phiq,
-                              long long phiq_bstride, const int* P, int Pmax,
+                              long long cap, int M, double* phiq,
+                              long long phiq_bstride, const double* fpart, int fnch,
+                              const double* zeta, const int* P, int Pmax,
                               int B, int m, double lambda,
                               double* dist, double* alpha, int* idx, int* meff,
                               int* esc_count, int* fail, const int* gate,
