@@ -267,7 +267,10 @@ rnp_status predict_core(rnp_ctx* c, const double* q, long long q_base, long long
   // captured sweep graph serves every later dataset size
   const int pm = Pmax(c) > 0 ? (int)std::max<long long>(Pmax(c), std::min<long long>(c->cap, 256))
                              : 0;
-  const double* fpart = nullptr;  // feature partials left for the ridge kernel
+  // the query's feature partials are finished inside the ridge kernel
+  // (except on the BF16 path); FP32 queries leave FP32 partials
+  float* fpart32 = reinterpret_cast<float*>(c->feat_part);
+  float* npart32 = reinterpret_cast<float*>(c->nn_part);
   if (c->fp32) {
     // mixed: FP32 query, FP32 features and FP32 distance screening
     CK(launch_scale_rows(c->g, q, src, nullptr, 1, c->sc, c->sr, nullptr, c->q32, qrows, c->B,
@@ -275,24 +278,27 @@ rnp_status predict_core(rnp_ctx* c, const double* q, long long q_base, long long
     if (c->bf16) {
       CK(launch_features_bf16(c->Abf, c->zeta, c->M, c->d, c->q32, qrows, c->B, phi_dst, prow,
                               c->feat_part, gate, c->st));
-      CK(launch_nn_partial32(c->q32, c->S32, c->cap, c->d, c->dP, pm, c->B, c->nn_part, gate,
+      CK(launch_nn_partial32(c->q32, c->S32, c->cap, c->d, c->dP, pm, c->B, npart32, gate,
                              c->st));
+      fpart32 = nullptr;
     } else {
-      CK(launch_query32(c->A32, c->M, c->d, c->q32, c->B, c->feat_part, c->S32, c->cap, c->dP,
-                        pm, c->nn_part, gate, c->st));
-      fpart = c->feat_part;
+      CK(launch_query32(c->A32, c->M, c->d, c->q32, c->B, fpart32, c->S32, c->cap, c->dP, pm,
+                        npart32, gate, c->st));
     }
+    CK(launch_topm_ridge32(npart32, nn_chunks(c->d), c->Phi, c->cap, c->M, phi_dst + phi_base,
+                           phi_bstride, fpart32, features_chunks(c->d), c->zeta, c->dP, pm, c->B,
+                           c->m, c->p.lambda, c->dist, c->alpha, c->idx, c->meff, c->flags + 0,
+                           c->flags + 1, gate, c->st));
   } else {
     CK(launch_scale_rows(c->g, q, src, nullptr, 1, c->sc, c->sr, c->qbuf, nullptr, qrows, c->B,
                          gate, c->st));
     CK(launch_query64(c->A, c->M, c->d, c->qbuf, c->B, c->feat_part, c->Sds, c->cap, c->dP, pm,
                       c->nn_part, gate, c->st));
-    fpart = c->feat_part;
+    CK(launch_topm_ridge(c->nn_part, nn_chunks(c->d), c->Phi, c->cap, c->M, phi_dst + phi_base,
+                         phi_bstride, c->feat_part, features_chunks(c->d), c->zeta, c->dP, pm,
+                         c->B, c->m, c->p.lambda, c->dist, c->alpha, c->idx, c->meff,
+                         c->flags + 0, c->flags + 1, gate, c->st));
   }
-  CK(launch_topm_ridge(c->nn_part, nn_chunks(c->d), c->Phi, c->cap, c->M, phi_dst + phi_base,
-                       phi_bstride, fpart, features_chunks(c->d), c->zeta, c->dP, pm, c->B, c->m,
-                       c->p.lambda, c->dist, c->alpha, c->idx, c->meff, c->flags + 0,
-                       c->flags + 1, gate, c->st));
   return RNP_OK;
 }
 

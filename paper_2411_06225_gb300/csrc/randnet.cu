@@ -201,10 +201,10 @@ static const int kFeatFW = 16;
 
 int features_chunks(long long d) { return (int)((d + kFeatCH - 1) / kFeatCH); }
 
-template <typename T>
+template <typename T, typename TP>
 __device__ __forceinline__ void feat_partial_body(T (&sS)[kFeatTR][kFeatCH], const T* A, int M,
                                                   long long d, const T* S, Rows rows, int R,
-                                                  double* part, int nch, const int* gate,
+                                                  TP* part, int nch, const int* gate,
                                                   int ch, int ry, int wz) {
   const int r0 = ry * kFeatTR;
   const int w0 = wz * kFeatFW;
@@ -243,7 +243,7 @@ __device__ __forceinline__ void feat_partial_body(T (&sS)[kFeatTR][kFeatCH], con
     if (lane == 0) {
 #pragma unroll
       for (int r = 0; r < kFeatTR; ++r)
-        if (r0 + r < R) part[((long long)(r0 + r) * M + w) * nch + ch] = (double)acc[r];
+        if (r0 + r < R) part[((long long)(r0 + r) * M + w) * nch + ch] = (TP)acc[r];
     }
   }
 }
@@ -254,8 +254,8 @@ __global__ void __launch_bounds__(256) k_feat_partial(const T* A, int M, long lo
                                                       double* part, int nch,
                                                       const int* gate) {
   __shared__ T sS[kFeatTR][kFeatCH];
-  feat_partial_body<T>(sS, A, M, d, S, rows, R, part, nch, gate, blockIdx.x, blockIdx.y,
-                       blockIdx.z);
+  feat_partial_body<T, double>(sS, A, M, d, S, rows, R, part, nch, gate, blockIdx.x, blockIdx.y,
+                               blockIdx.z);
 }
 
 __global__ void k_feat_finish(const double* part, int nch, int R, int M, const double* zeta,
@@ -318,7 +318,7 @@ int nn_chunks(long long d) { return (int)((d + nn_chunk_len(d) - 1) / nn_chunk_l
 template <typename T>
 __device__ __forceinline__ void nn_partial_body(const T* q, const T* S, long long cap,
                                                 long long d, long long chl, const int* P,
-                                                double* part, int nch, const int* gate,
+                                                T* part, int nch, const int* gate,
                                                 int ch, int by, int gy, int b) {
   if (gate && !gate[b]) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -344,14 +344,14 @@ __device__ __forceinline__ void nn_partial_body(const T* q, const T* S, long lon
     T acc = acc0 + acc1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) part[((long long)b * cap + p) * nch + ch] = (double)acc;
+    if (lane == 0) part[((long long)b * cap + p) * nch + ch] = acc;
   }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_nn_partial(const T* q, const T* S, long long cap,
                                                     long long d, long long chl,
-                                                    const int* P, double* part, int nch,
+                                                    const int* P, T* part, int nch,
                                                     const int* gate) {
   nn_partial_body<T>(q, S, cap, d, chl, P, part, nch, gate, blockIdx.x, blockIdx.y, gridDim.y,
                      blockIdx.z);
@@ -362,15 +362,15 @@ __global__ void __launch_bounds__(256) k_nn_partial(const T* q, const T* S, long
 // the rest the distance partials (grid nch_n x gy x B, flattened).
 template <typename T>
 __global__ void __launch_bounds__(256) k_query_partials(
-    const T* A, int M, long long d, const T* q, Rows qrows, int R, double* fpart, int fnch,
-    int nry, int nfb, const T* S, long long cap, long long chl, const int* P, double* npart,
+    const T* A, int M, long long d, const T* q, Rows qrows, int R, T* fpart, int fnch,
+    int nry, int nfb, const T* S, long long cap, long long chl, const int* P, T* npart,
     int nnch, int gy, const int* gate) {
   __shared__ T sS[kFeatTR][kFeatCH];
   int bid = blockIdx.x;
   if (bid < nfb) {
     const int ch = bid % fnch, rest = bid / fnch;
-    feat_partial_body<T>(sS, A, M, d, q, qrows, R, fpart, fnch, gate, ch, rest % nry,
-                         rest / nry);
+    feat_partial_body<T, T>(sS, A, M, d, q, qrows, R, fpart, fnch, gate, ch, rest % nry,
+                            rest / nry);
     return;
   }
   bid -= nfb;
@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(256) k_query_partials(
 
 template <typename T>
 static cudaError_t launch_nn_t(const T* q, const T* S, long long cap, long long d, const int* P,
-                               int Pmax, int B, double* part, const int* gate,
+                               int Pmax, int B, T* part, const int* gate,
                                cudaStream_t st) {
   if (Pmax <= 0 || B <= 0) return cudaSuccess;
   const int nch = nn_chunks(d);
@@ -401,15 +401,15 @@ cudaError_t launch_nn_partial(const double* q, const double* S, long long cap, l
 }
 
 cudaError_t launch_nn_partial32(const float* q, const float* S, long long cap, long long d,
-                                const int* P, int Pmax, int B, double* part, const int* gate,
+                                const int* P, int Pmax, int B, float* part, const int* gate,
                                 cudaStream_t st) {
   return launch_nn_t<float>(q, S, cap, d, P, Pmax, B, part, gate, st);
 }
 
 template <typename T>
 static cudaError_t launch_query_t(const T* A, int M, long long d, const T* q, int B,
-                                  double* fpart, const T* S, long long cap, const int* P,
-                                  int Pmax, double* npart, const int* gate, cudaStream_t st) {
+                                  T* fpart, const T* S, long long cap, const int* P,
+                                  int Pmax, T* npart, const int* gate, cudaStream_t st) {
   if (B <= 0) return cudaSuccess;
   const int fnch = features_chunks(d);
   const int nry = (B + kFeatTR - 1) / kFeatTR, nwz = (M + kFeatFW - 1) / kFeatFW;
@@ -433,8 +433,8 @@ cudaError_t launch_query64(const double* A, int M, long long d, const double* q,
 }
 
 cudaError_t launch_query32(const float* A, int M, long long d, const float* q, int B,
-                           double* fpart, const float* S, long long cap, const int* P,
-                           int Pmax, double* npart, const int* gate, cudaStream_t st) {
+                           float* fpart, const float* S, long long cap, const int* P,
+                           int Pmax, float* npart, const int* gate, cudaStream_t st) {
   return launch_query_t<float>(A, M, d, q, B, fpart, S, cap, P, Pmax, npart, gate, st);
 }
 
@@ -443,16 +443,94 @@ cudaError_t launch_query32(const float* A, int M, long long d, const float* q, i
 // ---------------------------------------------------------------------------
 // Distances are sums of squares (>= 0 or NaN), so their bit patterns order
 // like the values and a NaN orders after +inf: the selection compares 64-bit
-// integer keys (ties -> lower index).
-__device__ __forceinline__ bool key_less(unsigned long long a, int ia, unsigned long long b,
-                                         int ib) {
-  return a < b || (a == b && ia < ib);
+// integer keys (ties -> lower index).  Minimum of (key, index) over a warp
+// with three 32-bit reductions; lanes without a candidate pass key ~0.
+__device__ __forceinline__ void warp_min_key(unsigned long long key, unsigned idx,
+                                             unsigned long long* okey, unsigned* oidx) {
+  const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
+  const unsigned mhi = __reduce_min_sync(0xffffffffu, hi);
+  const unsigned mlo = __reduce_min_sync(0xffffffffu, hi == mhi ? lo : 0xffffffffu);
+  *oidx = __reduce_min_sync(0xffffffffu, (hi == mhi && lo == mlo) ? idx : 0xffffffffu);
+  *okey = ((unsigned long long)mhi << 32) | mlo;
 }
 
-__global__ void __launch_bounds__(256) k_topm_ridge(const double* part, int nch,
+// Cholesky solve of (K + lam I) x = r for a small system held in registers
+// (n <= 4 after unrolling): one reciprocal square root per pivot scales its
+// column and both triangular solves.  Returns false on a non-positive pivot.
+template <int N>
+__device__ __forceinline__ bool chol_small(const double* Kraw, const double* r, double lam,
+                                           double* x) {
+  double L[N][N], li[N], y[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    double s = __dadd_rn(Kraw[j * RNP_MAX_M + j], lam);
+#pragma unroll
+    for (int k = 0; k < j; ++k) s = __dsub_rn(s, __dmul_rn(L[j][k], L[j][k]));
+    if (!(s > 0.0)) return false;
+    const double inv = rsqrt(s);
+    li[j] = inv;
+#pragma unroll
+    for (int i = j + 1; i < N; ++i) {
+      double t = Kraw[i * RNP_MAX_M + j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) t = __dsub_rn(t, __dmul_rn(L[i][k], L[j][k]));
+      L[i][j] = __dmul_rn(t, inv);
+    }
+    L[j][j] = __dmul_rn(s, inv);
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    double t = r[i];
+#pragma unroll
+    for (int k = 0; k < i; ++k) t = __dsub_rn(t, __dmul_rn(L[i][k], y[k]));
+    y[i] = __dmul_rn(t, li[i]);
+  }
+#pragma unroll
+  for (int i = N - 1; i >= 0; --i) {
+    double t = y[i];
+#pragma unroll
+    for (int k = i + 1; k < N; ++k) t = __dsub_rn(t, __dmul_rn(L[k][i], x[k]));
+    x[i] = __dmul_rn(t, li[i]);
+  }
+  return true;
+}
+
+// The same for any n <= RNP_MAX_M with the factor in shared memory.
+__device__ bool chol_general(const double* Kraw, const double* r, double lam, int n, double* L,
+                             double* li, double* y, double* x) {
+  for (int j = 0; j < n; ++j) {
+    double s = __dadd_rn(Kraw[j * RNP_MAX_M + j], lam);
+    for (int k = 0; k < j; ++k) s = __dsub_rn(s, __dmul_rn(L[j * RNP_MAX_M + k], L[j * RNP_MAX_M + k]));
+    if (!(s > 0.0)) return false;
+    const double inv = rsqrt(s);
+    li[j] = inv;
+    for (int i = j + 1; i < n; ++i) {
+      double t = Kraw[i * RNP_MAX_M + j];
+      for (int k = 0; k < j; ++k) t = __dsub_rn(t, __dmul_rn(L[i * RNP_MAX_M + k], L[j * RNP_MAX_M + k]));
+      L[i * RNP_MAX_M + j] = __dmul_rn(t, inv);
+    }
+    L[j * RNP_MAX_M + j] = __dmul_rn(s, inv);
+  }
+  for (int i = 0; i < n; ++i) {
+    double t = r[i];
+    for (int k = 0; k < i; ++k) t = __dsub_rn(t, __dmul_rn(L[i * RNP_MAX_M + k], y[k]));
+    y[i] = __dmul_rn(t, li[i]);
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double t = y[i];
+    for (int k = i + 1; k < n; ++k) t = __dsub_rn(t, __dmul_rn(L[k * RNP_MAX_M + i], x[k]));
+    x[i] = __dmul_rn(t, li[i]);
+  }
+  return true;
+}
+
+// TP: type of the chunk partials (double in the FP64 path, float where the
+// query was computed in FP32; their sums are kept in TP).
+template <typename TP>
+__global__ void __launch_bounds__(256) k_topm_ridge(const TP* part, int nch,
                                                     const double* Phi, long long cap, int M,
                                                     double* phiq, long long phiq_bstride,
-                                                    const double* fpart, int fnch,
+                                                    const TP* fpart, int fnch,
                                                     const double* zeta, const int* Pn, int m,
                                                     double lambda, double* dist, double* alpha,
                                                     int* idx, int* meff, int* esc_count,
@@ -461,29 +539,30 @@ __global__ void __launch_bounds__(256) k_topm_ridge(const double* part, int nch,
   if (gate && !gate[b]) return;
   const int P = Pn[b];
   const int me = m < P ? m : P;
+  constexpr int kWarps = 8;  // blockDim.x == 256
   __shared__ int sel[RNP_MAX_M];
-  __shared__ unsigned long long wk[32];
-  __shared__ int wi[32];
+  __shared__ unsigned long long ck[kWarps * RNP_MAX_M];
+  __shared__ unsigned ci[kWarps * RNP_MAX_M];
   __shared__ double Kraw[RNP_MAX_M * RNP_MAX_M];
-  __shared__ double L[RNP_MAX_M * RNP_MAX_M];
-  __shared__ double rhs[RNP_MAX_M], y[RNP_MAX_M], x[RNP_MAX_M], linv[RNP_MAX_M];
+  __shared__ double Lsh[RNP_MAX_M * RNP_MAX_M];
+  __shared__ double rhs[RNP_MAX_M], ysh[RNP_MAX_M], xsh[RNP_MAX_M], lish[RNP_MAX_M];
   double* pq = phiq + (long long)b * phiq_bstride;
   // query features (when their partials are given): the chunk partials in
-  // chunk order, + zeta, ReLU -- the arithmetic of k_feat_finish
+  // chunk order, + zeta, ReLU
   if (fpart) {
     for (int w = threadIdx.x; w < M; w += blockDim.x) {
-      const double* fp = fpart + ((long long)b * M + w) * fnch;
-      double acc = 0.0;
+      const TP* fp = fpart + ((long long)b * M + w) * fnch;
+      TP acc = TP(0);
       for (int k = 0; k < fnch; ++k) acc = acc + fp[k];
-      const double v = acc + zeta[w];
+      const double v = (double)acc + zeta[w];
       pq[w] = v > 0.0 ? v : 0.0;
     }
   }
   // distances: four interleaved partial sums over the chunks, then combined
   double* db = dist + (long long)b * cap;
   for (int p = threadIdx.x; p < P; p += blockDim.x) {
-    const double* pp = part + ((long long)b * cap + p) * nch;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    const TP* pp = part + ((long long)b * cap + p) * nch;
+    TP a0 = TP(0), a1 = TP(0), a2 = TP(0), a3 = TP(0);
     int k = 0;
     for (; k + 3 < nch; k += 4) {
       a0 = a0 + pp[k];
@@ -492,42 +571,56 @@ __global__ void __launch_bounds__(256) k_topm_ridge(const double* part, int nch,
       a3 = a3 + pp[k + 3];
     }
     for (; k < nch; ++k) a0 = a0 + pp[k];
-    db[p] = (a0 + a1) + (a2 + a3);
+    db[p] = (double)((a0 + a1) + (a2 + a3));
   }
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int l = 0; l < me; ++l) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // m nearest: every warp selects its own me best among its candidates
+  // (p = warp * 32 + lane + k * 256), then warp 0 selects among those
+  for (int r = 0; r < me; ++r) {
     unsigned long long bk = ~0ULL;
-    int bi = 0x7fffffff;
+    unsigned bi = 0xffffffffu;
     for (int p = threadIdx.x; p < P; p += blockDim.x) {
       bool taken = false;
-      for (int k = 0; k < l; ++k) taken |= (sel[k] == p);
+      for (int k = 0; k < r; ++k) taken |= (ci[warp * RNP_MAX_M + k] == (unsigned)p);
       if (taken) continue;
       const unsigned long long v = (unsigned long long)__double_as_longlong(db[p]);
-      if (key_less(v, p, bk, bi)) { bk = v; bi = p; }
+      if (v < bk || (v == bk && (unsigned)p < bi)) { bk = v; bi = (unsigned)p; }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (key_less(ok, oi, bk, bi)) { bk = ok; bi = oi; }
-    }
-    if (lane == 0) { wk[warp] = bk; wi[warp] = bi; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      unsigned long long xk = wk[0];
-      int xi = wi[0];
-      for (int k = 1; k < nw; ++k)
-        if (key_less(wk[k], wi[k], xk, xi)) { xk = wk[k]; xi = wi[k]; }
-      sel[l] = xi;
-    }
-    __syncthreads();
+    unsigned long long wkey;
+    unsigned widx;
+    warp_min_key(bk, bi, &wkey, &widx);
+    if (lane == 0) { ck[warp * RNP_MAX_M + r] = wkey; ci[warp * RNP_MAX_M + r] = widx; }
+    __syncwarp();
   }
+  __syncthreads();
+  if (warp == 0) {
+    const int nc = kWarps * me;
+    for (int r = 0; r < me; ++r) {
+      unsigned long long bk = ~0ULL;
+      unsigned bi = 0xffffffffu;
+      for (int c = lane; c < nc; c += 32) {
+        const int w = c / me, k = c - w * me;
+        const unsigned long long v = ck[w * RNP_MAX_M + k];
+        const unsigned id = ci[w * RNP_MAX_M + k];
+        bool taken = false;
+        for (int t = 0; t < r; ++t) taken |= (sel[t] == (int)id);
+        if (taken || id == 0xffffffffu) continue;
+        if (v < bk || (v == bk && id < bi)) { bk = v; bi = id; }
+      }
+      unsigned long long wkey;
+      unsigned widx;
+      warp_min_key(bk, bi, &wkey, &widx);
+      if (lane == 0) sel[r] = (int)widx;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
   // Gram entries K[i][j] = sum_w X_i,w X_j,w (i >= j) and rhs_i = X_i . phi_q:
   // one warp per entry, lanes stride w, fixed butterfly reduction.
   const double* X = Phi + (long long)b * cap * M;
   const int nK = me * (me + 1) / 2;
-  for (int t = warp; t < nK + me; t += nw) {
+  for (int t = warp; t < nK + me; t += kWarps) {
     const double *xa, *xb;
     int i, j = -1;
     if (t < nK) {
@@ -555,25 +648,18 @@ __global__ void __launch_bounds__(256) k_topm_ridge(const double* part, int nch,
   meff[b] = me;
   for (int l = 0; l < me; ++l) idx[b * RNP_MAX_M + l] = sel[l];
   if (me == 0) return;
-  // Cholesky of K + lambda I with one division per column (the reciprocal
-  // of the pivot multiplies the column and both triangular solves)
+  // Cholesky of K + lambda I; lambda x10 on a non-positive pivot
   double lam = lambda;
-  int ok = 0, tries = 0;
+  double x[4];
+  bool ok = false;
+  int tries = 0;
   for (tries = 0; tries <= 4 && !ok; ++tries) {
-    ok = 1;
-    for (int j = 0; j < me && ok; ++j) {
-      double s = __dadd_rn(Kraw[j * RNP_MAX_M + j], lam);
-      for (int k = 0; k < j; ++k) s = __dsub_rn(s, __dmul_rn(L[j * RNP_MAX_M + k], L[j * RNP_MAX_M + k]));
-      if (!(s > 0.0)) { ok = 0; break; }
-      const double ljj = __dsqrt_rn(s);
-      const double inv = __ddiv_rn(1.0, ljj);
-      L[j * RNP_MAX_M + j] = ljj;
-      linv[j] = inv;
-      for (int i = j + 1; i < me; ++i) {
-        double t = Kraw[i * RNP_MAX_M + j];
-        for (int k = 0; k < j; ++k) t = __dsub_rn(t, __dmul_rn(L[i * RNP_MAX_M + k], L[j * RNP_MAX_M + k]));
-        L[i * RNP_MAX_M + j] = __dmul_rn(t, inv);
-      }
+    switch (me) {
+      case 1: ok = chol_small<1>(Kraw, rhs, lam, x); break;
+      case 2: ok = chol_small<2>(Kraw, rhs, lam, x); break;
+      case 3: ok = chol_small<3>(Kraw, rhs, lam, x); break;
+      case 4: ok = chol_small<4>(Kraw, rhs, lam, x); break;
+      default: ok = chol_general(Kraw, rhs, lam, me, Lsh, lish, ysh, xsh);
     }
     if (!ok) lam = __dmul_rn(lam, 10.0);
   }
@@ -583,17 +669,21 @@ __global__ void __launch_bounds__(256) k_topm_ridge(const double* part, int nch,
     return;
   }
   if (tries - 1 > 0) atomicAdd(esc_count, tries - 1);
-  for (int i = 0; i < me; ++i) {
-    double t = rhs[i];
-    for (int k = 0; k < i; ++k) t = __dsub_rn(t, __dmul_rn(L[i * RNP_MAX_M + k], y[k]));
-    y[i] = __dmul_rn(t, linv[i]);
-  }
-  for (int i = me - 1; i >= 0; --i) {
-    double t = y[i];
-    for (int k = i + 1; k < me; ++k) t = __dsub_rn(t, __dmul_rn(L[k * RNP_MAX_M + i], x[k]));
-    x[i] = __dmul_rn(t, linv[i]);
-  }
-  for (int l = 0; l < me; ++l) alpha[b * RNP_MAX_M + l] = x[l];
+  for (int l = 0; l < me; ++l) alpha[b * RNP_MAX_M + l] = me <= 4 ? x[l] : xsh[l];
+}
+
+template <typename TP>
+static cudaError_t launch_topm_t(const TP* part, int nch, const double* Phi, long long cap,
+                                 int M, double* phiq, long long phiq_bstride, const TP* fpart,
+                                 int fnch, const double* zeta, const int* P, int B, int m,
+                                 double lambda, double* dist, double* alpha, int* idx,
+                                 int* meff, int* esc_count, int* fail, const int* gate,
+                                 cudaStream_t st) {
+  count_launches(1);
+  k_topm_ridge<TP><<<B, 256, 0, st>>>(part, nch, Phi, cap, M, phiq, phiq_bstride, fpart, fnch,
+                                      zeta, P, m, lambda, dist, alpha, idx, meff, esc_count,
+                                      fail, gate);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_topm_ridge(const double* part, int nch, const double* Phi, long long cap,
@@ -603,10 +693,19 @@ cudaError_t launch_topm_ridge(const double* part, int nch, const double* Phi, lo
                               int* meff, int* esc_count, int* fail, const int* gate,
                               cudaStream_t st) {
   (void)Pmax;
-  count_launches(1);
-  k_topm_ridge<<<B, 256, 0, st>>>(part, nch, Phi, cap, M, phiq, phiq_bstride, fpart, fnch, zeta,
-                                  P, m, lambda, dist, alpha, idx, meff, esc_count, fail, gate);
-  return cudaGetLastError();
+  return launch_topm_t<double>(part, nch, Phi, cap, M, phiq, phiq_bstride, fpart, fnch, zeta, P,
+                               B, m, lambda, dist, alpha, idx, meff, esc_count, fail, gate, st);
+}
+
+cudaError_t launch_topm_ridge32(const float* part, int nch, const double* Phi, long long cap,
+                                int M, double* phiq, long long phiq_bstride, const float* fpart,
+                                int fnch, const double* zeta, const int* P, int Pmax, int B,
+                                int m, double lambda, double* dist, double* alpha, int* idx,
+                                int* meff, int* esc_count, int* fail, const int* gate,
+                                cudaStream_t st) {
+  (void)Pmax;
+  return launch_topm_t<float>(part, nch, Phi, cap, M, phiq, phiq_bstride, fpart, fnch, zeta, P,
+                              B, m, lambda, dist, alpha, idx, meff, esc_count, fail, gate, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -162,7 +162,7 @@ cudaError_t launch_nn_partial(const double* q, const double* S, long long cap,
                               double* part, const int* gate, cudaStream_t st);
 cudaError_t launch_nn_partial32(const float* q, const float* S, long long cap,
                                 long long d, const int* P, int Pmax, int B,
-                                double* part, const int* gate, cudaStream_t st);
+                                float* part, const int* gate, cudaStream_t st);
 int nn_chunks(long long d);
 
 // Both partial sums of a RandNet query in one launch: the feature partials
@@ -172,8 +172,8 @@ cudaError_t launch_query64(const double* A, int M, long long d, const double* q,
                            double* fpart, const double* S, long long cap, const int* P,
                            int Pmax, double* npart, const int* gate, cudaStream_t st);
 cudaError_t launch_query32(const float* A, int M, long long d, const float* q, int B,
-                           double* fpart, const float* S, long long cap, const int* P,
-                           int Pmax, double* npart, const int* gate, cudaStream_t st);
+                           float* fpart, const float* S, long long cap, const int* P,
+                           int Pmax, float* npart, const int* gate, cudaStream_t st);
 
 // Per member: (if fpart != null) finish the query features phi_q from their
 // chunk partials into phiq[b]; finish distances, select the m nearest (ties
@@ -188,6 +188,15 @@ cudaError_t launch_topm_ridge(const double* part, int nch, const double* Phi,
                               double* dist, double* alpha, int* idx, int* meff,
                               int* esc_count, int* fail, const int* gate,
                               cudaStream_t st);
+// The same with FP32 chunk partials (from launch_query32 / launch_nn_partial32).
+cudaError_t launch_topm_ridge32(const float* part, int nch, const double* Phi,
+                                long long cap, int M, double* phiq,
+                                long long phiq_bstride, const float* fpart, int fnch,
+                                const double* zeta, const int* P, int Pmax,
+                                int B, int m, double lambda,
+                                double* dist, double* alpha, int* idx, int* meff,
+                                int* esc_count, int* fail, const int* gate,
+                                cudaStream_t st);
 
 // out[b] = g[b] + sum_l alpha_l Y[b][idx_l]  (g may be null: out = sum).
 // If err != null: err[b] = max |out_new - out_old| over the state (the old
