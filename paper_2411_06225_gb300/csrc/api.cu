@@ -54,6 +54,8 @@ struct rnp_ctx {
   long long* d_items = nullptr;   // src, dst, soff, phioff tables (4 * itemcap)
   int* d_app = nullptr;           // b, j, p (3 * itemcap)
   int* d_gate = nullptr;          // (N + 1) * B
+  long long* d_qsrc = nullptr;    // [B] first sweep query of each member (offset in U)
+  int* d_qgate = nullptr;         // [B] member has a sweep this iteration
   int itemcap = 0;
   int feat_rows_cap = 0;
 
@@ -61,6 +63,8 @@ struct rnp_ctx {
   long long* h_items = nullptr;   // pinned
   int* h_app = nullptr;           // pinned
   int* h_gate = nullptr;          // pinned
+  long long* h_qsrc = nullptr;    // pinned [B]
+  int* h_qgate = nullptr;         // pinned [B]
   unsigned long long* h_err = nullptr;  // pinned (B * (N+1))
   int* h_flags = nullptr;         // pinned (4)
   std::vector<int> P;             // pairs per member
@@ -180,12 +184,14 @@ void destroy_buffers(rnp_ctx* c) {
                   c->Yds, c->Phi, c->A, c->zeta, c->sc, c->sr, c->scale_work, c->feat_part,
                   c->nn_part, c->dist, c->alpha, c->idx, c->meff, c->flags, c->dP, c->err,
                   c->plain_work, c->d_items, c->d_app, c->d_gate, c->A32, c->S32, c->q32,
-                  c->d_mask, c->Abf, c->tc_part};
+                  c->d_mask, c->Abf, c->tc_part, c->d_qsrc, c->d_qgate};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->h_items) cudaFreeHost(c->h_items);
   if (c->h_app) cudaFreeHost(c->h_app);
   if (c->h_gate) cudaFreeHost(c->h_gate);
+  if (c->h_qsrc) cudaFreeHost(c->h_qsrc);
+  if (c->h_qgate) cudaFreeHost(c->h_qgate);
   if (c->h_err) cudaFreeHost(c->h_err);
   if (c->h_flags) cudaFreeHost(c->h_flags);
   if (c->h_mask) cudaFreeHost(c->h_mask);
@@ -259,7 +265,7 @@ int Pmax(const rnp_ctx* c) {
 // meff are left on the device for the update kernel.
 rnp_status predict_core(rnp_ctx* c, const double* q, long long q_base, long long q_bstride,
                         double* phi_dst, long long phi_base, long long phi_bstride,
-                        const int* gate) {
+                        const int* gate, bool q_ready = false) {
   Rows src{nullptr, q_base, q_bstride};
   Rows qrows{nullptr, 0, c->d};
   Rows prow{nullptr, phi_base, phi_bstride};
@@ -273,8 +279,9 @@ rnp_status predict_core(rnp_ctx* c, const double* q, long long q_base, long long
   float* npart32 = reinterpret_cast<float*>(c->nn_part);
   if (c->fp32) {
     // mixed: FP32 query, FP32 features and FP32 distance screening
-    CK(launch_scale_rows(c->g, q, src, nullptr, 1, c->sc, c->sr, nullptr, c->q32, qrows, c->B,
-                         gate, c->st));
+    if (!q_ready)
+      CK(launch_scale_rows(c->g, q, src, nullptr, 1, c->sc, c->sr, nullptr, c->q32, qrows, c->B,
+                           gate, c->st));
     if (c->bf16) {
       CK(launch_features_bf16(c->Abf, c->zeta, c->M, c->d, c->q32, qrows, c->B, phi_dst, prow,
                               c->feat_part, gate, c->st));
@@ -290,8 +297,9 @@ rnp_status predict_core(rnp_ctx* c, const double* q, long long q_base, long long
                            c->m, c->p.lambda, c->dist, c->alpha, c->idx, c->meff, c->flags + 0,
                            c->flags + 1, gate, c->st));
   } else {
-    CK(launch_scale_rows(c->g, q, src, nullptr, 1, c->sc, c->sr, c->qbuf, nullptr, qrows, c->B,
-                         gate, c->st));
+    if (!q_ready)
+      CK(launch_scale_rows(c->g, q, src, nullptr, 1, c->sc, c->sr, c->qbuf, nullptr, qrows, c->B,
+                           gate, c->st));
     CK(launch_query64(c->A, c->M, c->d, c->qbuf, c->B, c->feat_part, c->Sds, c->cap, c->dP, pm,
                       c->nn_part, gate, c->st));
     CK(launch_topm_ridge(c->nn_part, nn_chunks(c->d), c->Phi, c->cap, c->M, phi_dst + phi_base,
@@ -321,18 +329,23 @@ rnp_status sweep_step(rnp_ctx* c, double* U, long long ubs, int i, double* Gc,
   if ((s = run_stencil(c, false, U, c->gbuf, Gc, it, c->st2))) return s;
   CK(cudaEventRecord(c->evj, c->st2));
   if (c->randnet) {
+    // the scaled query U[b][i-1] is already in q32 / qbuf: scaled before the
+    // sweep for its first step, by the previous step's update otherwise
     if (Gc) {
       // the solve caches the query's features as the next dataset row
       if ((s = predict_core(c, U, (long long)(i - 1) * d, ubs, c->phic, (long long)(i - 1) * c->M,
-                            (long long)c->N * c->M, gate)))
+                            (long long)c->N * c->M, gate, true)))
         return s;
-    } else if ((s = predict_core(c, U, (long long)(i - 1) * d, ubs, c->phiq, 0, c->M, gate))) {
+    } else if ((s = predict_core(c, U, (long long)(i - 1) * d, ubs, c->phiq, 0, c->M, gate,
+                                 true))) {
       return s;
     }
     CK(cudaStreamWaitEvent(c->st, c->evj, 0));
+    const QueryOut qo{c->sc, c->sr, c->g.n, c->fp32 ? nullptr : c->qbuf,
+                      c->fp32 ? c->q32 : nullptr};
     CK(launch_update(c->gbuf, d, c->Yds, c->cap, d, c->alpha, c->idx, c->meff,
                      U + (long long)i * d, ubs, err ? err + i : nullptr, c->N + 1, c->flags + 2,
-                     c->B, gate, c->st));
+                     c->B, gate, c->st, qo));
   } else {
     CK(cudaStreamWaitEvent(c->st, c->evj, 0));
     CK(launch_update_para(c->gbuf, d, c->Yv + (long long)(i - 1) * d, nb, d,
@@ -578,6 +591,10 @@ rnp_status rnp_create(const rnp_problem* prob, void* cuda_stream, rnp_ctx** out)
   ok &= dalloc(&c->d_app, (size_t)3 * c->itemcap) == cudaSuccess;
   ok &= dalloc(&c->d_gate, (size_t)(N + 1) * B) == cudaSuccess;
   ok &= dalloc(&c->d_mask, (size_t)B) == cudaSuccess;
+  ok &= dalloc(&c->d_qsrc, (size_t)B) == cudaSuccess;
+  ok &= dalloc(&c->d_qgate, (size_t)B) == cudaSuccess;
+  ok &= cudaMallocHost((void**)&c->h_qsrc, sizeof(long long) * B) == cudaSuccess;
+  ok &= cudaMallocHost((void**)&c->h_qgate, sizeof(int) * B) == cudaSuccess;
   ok &= cudaMallocHost((void**)&c->h_mask, sizeof(int) * B) == cudaSuccess;
   ok &= cudaMallocHost((void**)&c->h_items, sizeof(long long) * 4 * c->itemcap) == cudaSuccess;
   ok &= cudaMallocHost((void**)&c->h_app, sizeof(int) * 3 * c->itemcap) == cudaSuccess;
@@ -840,6 +857,10 @@ rnp_status rnp_coarse_sweep(rnp_ctx* c, int first, const double* U_first, double
     if ((s = ensure_scaling_identity(c))) return s;
   }
   CK(cudaMemsetAsync(c->flags, 0, sizeof(int) * 4, c->st));
+  if (use_fhat && first < c->N)  // the first step's scaled query (later: from the update)
+    CK(launch_scale_rows(c->g, U, Rows{nullptr, (long long)first * d, sb}, nullptr, 1, c->sc,
+                         c->sr, c->fp32 ? nullptr : c->qbuf, c->fp32 ? c->q32 : nullptr,
+                         Rows{nullptr, 0, d}, c->B, nullptr, c->st));
   for (int i = first + 1; i <= c->N; ++i) {
     if (!use_fhat) {
       Items it = affine(c->B, (long long)(i - 1) * d, sb, (long long)i * d, sb, nullptr);
@@ -1001,6 +1022,20 @@ rnp_status iterate_once(rnp_ctx* c, rnp_stats* st, int* n_active) {
   int imin = N + 1;
   for (int b = 0; b < B; ++b)
     if (active(b)) imin = std::min(imin, L[b] + 2);
+  if (c->randnet && imin <= N) {
+    // the first step's scaled query U[b][L+1]; later steps get theirs from
+    // the update of the step before
+    for (int b = 0; b < B; ++b) {
+      c->h_qgate[b] = (active(b) && L[b] + 2 <= N) ? 1 : 0;
+      c->h_qsrc[b] = (long long)b * sb + (long long)(L[b] + 1) * d;
+    }
+    CK(cudaMemcpyAsync(c->d_qsrc, c->h_qsrc, sizeof(long long) * B, cudaMemcpyHostToDevice,
+                       c->st));
+    CK(cudaMemcpyAsync(c->d_qgate, c->h_qgate, sizeof(int) * B, cudaMemcpyHostToDevice, c->st));
+    CK(launch_scale_rows(c->g, c->U, Rows{c->d_qsrc, 0, 0}, nullptr, 1, c->sc, c->sr,
+                         c->fp32 ? nullptr : c->qbuf, c->fp32 ? c->q32 : nullptr,
+                         Rows{nullptr, 0, d}, B, c->d_qgate, c->st));
+  }
   if (imin <= N && (s = solve_sweep(c, imin))) return s;
   CK(cudaEventRecord(c->ev[3], c->st));
   CK(cudaMemcpyAsync(c->h_err, c->err, sizeof(unsigned long long) * B * (N + 1),

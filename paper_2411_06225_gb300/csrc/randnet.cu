@@ -734,7 +734,7 @@ __global__ void __launch_bounds__(256) k_update(const double* g, long long g_bst
                                                 const int* meff, double* out,
                                                 long long out_bstride, unsigned long long* err,
                                                 long long err_bstride, int* nonfinite,
-                                                const int* gate) {
+                                                const int* gate, QueryOut qo) {
   const int b = blockIdx.y;
   if (gate && !gate[b]) return;
   const int me = meff[b];
@@ -760,6 +760,13 @@ __global__ void __launch_bounds__(256) k_update(const double* g, long long g_bst
     }
     bad |= !isfinite(v);
     ob[j] = v;
+    if (qo.q64 || qo.q32) {
+      // the next step's scaled query, as k_scale_rows computes it
+      const int q = (int)(j / qo.n);
+      const double sv = __ddiv_rn(__dsub_rn(v, qo.c[b * 3 + q]), qo.r[b * 3 + q]);
+      if (qo.q64) qo.q64[(long long)b * d + j] = sv;
+      if (qo.q32) qo.q32[(long long)b * d + j] = (float)sv;
+    }
   }
   if (bad) atomicExch(nonfinite, 1);
   if (err) block_max_to(err + (long long)b * err_bstride, emax);
@@ -804,10 +811,11 @@ cudaError_t launch_update(const double* g, long long g_bstride, const double* Y,
                           long long cap, long long d, const double* alpha, const int* idx,
                           const int* meff, double* out, long long out_bstride,
                           unsigned long long* err, long long err_bstride, int* nonfinite,
-                          int B, const int* gate, cudaStream_t st) {
+                          int B, const int* gate, cudaStream_t st, QueryOut qo) {
   count_launches(1);
   k_update<<<update_grid(d, B), 256, 0, st>>>(g, g_bstride, Y, cap, d, alpha, idx, meff, out,
-                                              out_bstride, err, err_bstride, nonfinite, gate);
+                                              out_bstride, err, err_bstride, nonfinite, gate,
+                                              qo);
   return cudaGetLastError();
 }
 

@@ -198,6 +198,17 @@ cudaError_t launch_topm_ridge32(const float* part, int nch, const double* Phi,
                                 int* esc_count, int* fail, const int* gate,
                                 cudaStream_t st);
 
+// Optional second output of the update: the new state scaled per species,
+// (out - c[b][q]) / r[b][q] (n cells per species), written to q64[b] and/or
+// q32[b] (member stride d) -- the scaled query of the next sweep step.
+struct QueryOut {
+  const double* c;
+  const double* r;
+  long long n;
+  double* q64;
+  float* q32;
+};
+
 // out[b] = g[b] + sum_l alpha_l Y[b][idx_l]  (g may be null: out = sum).
 // If err != null: err[b] = max |out_new - out_old| over the state (the old
 // value is read before it is overwritten), and nonfinite is set on NaN/Inf.
@@ -207,7 +218,7 @@ cudaError_t launch_update(const double* g, long long g_bstride,
                           double* out, long long out_bstride,
                           unsigned long long* err, long long err_bstride,
                           int* nonfinite, int B, const int* gate,
-                          cudaStream_t st);
+                          cudaStream_t st, QueryOut qo = QueryOut{});
 
 // Parareal (Eq. 4) update: out[b] = g[b] + Yv[b]; err / nonfinite as above.
 cudaError_t launch_update_para(const double* g, long long g_bstride,

@@ -678,7 +678,10 @@ __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant_
   const int xsw = nx / PX;
   const int xl = (int)(threadIdx.x & 31) & (xsw - 1);
   const int xwest = (xl + xsw - 1) & (xsw - 1), xeast = (xl + 1) & (xsw - 1);
-  const unsigned xmask = blockDim.x >= 32 ? 0xffffffffu : ((1u << blockDim.x) - 1u);
+  // lanes present in this warp (the last warp of a block whose size is not
+  // a multiple of 32 is partial; it still holds whole x-rows)
+  const int wl = min(32, (int)blockDim.x - (int)(threadIdx.x & ~31u));
+  const unsigned xmask = wl >= 32 ? 0xffffffffu : ((1u << wl) - 1u);
 
   // halo targets: my first row is the previous rank's ghost row nloc, my
   // last row the next rank's ghost row -1 (buffer 0; +boff for buffer 1)
