@@ -434,8 +434,8 @@ rnp_status read_flags(rnp_ctx* c, int* esc, int* failf, int* nonfinite) {
 
 // Times every launchable stencil tiling for the fine step (all B N slices)
 // and the coarse step (one item per member) on the context's own buffers,
-// a few steps each after one untimed launch, and keeps the fastest.  The
-// cost of a step does not depend on the state's values.
+// a few dozen steps each, best of four after one untimed launch, and keeps
+// the fastest.  The cost of a step does not depend on the state's values.
 rnp_status autotune_stencils(rnp_ctx* c) {
   const int B = c->B, N = c->N;
   const long long d = c->d, sb = (long long)(N + 1) * d;
@@ -447,13 +447,15 @@ rnp_status autotune_stencils(rnp_ctx* c) {
     StencilCfg cands[64];
     const int n = list_stencil_cfgs(c->g, c->fp32, nitems, cands, 64);
     if (n <= 1) continue;
-    const int steps = std::min(fine ? c->p.nF : c->p.nG, fine ? 16 : 8);
+    // long enough (about half a millisecond for a fine step) that launch and
+    // cluster-scheduling noise do not decide the ranking
+    const int steps = std::min(fine ? c->p.nF : c->p.nG, fine ? 64 : 16);
     Items it = affine(nitems, 0, d, 0, d, nullptr);
     float best = 1e30f;
     int besti = -1;
     for (int k = 0; k < n; ++k) {
       float tmin = 1e30f;
-      for (int rep = 0; rep < 3; ++rep) {
+      for (int rep = 0; rep < 5; ++rep) {
         CK(cudaEventRecord(c->ev[4], c->st));
         CK(launch_stencil_fused(c->g, c->coef, c->fp32, fine ? SCHEME_RK4 : c->schemeG, steps,
                                 fine ? c->dtF : c->dtG, c->U, c->Fv, nullptr, it, cands[k],

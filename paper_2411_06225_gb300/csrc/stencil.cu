@@ -151,11 +151,11 @@ static int round_R(long long cells_per_thread) {
 
 static size_t smem_bytes(const Geom& g, bool fp32, int CS) {
   const long long ncell = (long long)(g.outer / CS) * g.plane;
-  // FP64 kernel: two stage buffers; mixed kernel: two stage buffers and the
-  // low words, each with two ghost rows, then two mbarriers, the 16-byte
-  // halo target table and two abort flags
+  // FP64 kernel: two stage buffers; mixed kernel: two stage buffers with two
+  // ghost rows each, the low words, then two mbarriers, the 16-byte halo
+  // target table and two abort flags
   if (!fp32) return 2 * (size_t)g.ncomp * ncell * 8;
-  const size_t f = 3 * (size_t)g.ncomp * (ncell + 2 * g.plane) * 4;
+  const size_t f = (2 * (size_t)g.ncomp * (ncell + 2 * g.plane) + (size_t)g.ncomp * ncell) * 4;
   return ((f + 15) & ~(size_t)15) + 48;
 }
 

@@ -521,6 +521,7 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
   const float* kk = P.kf;
   const float dt = P.fdt, h2 = P.fh2, h6 = P.fh6;
   constexpr int NC = KT<KP>::NC, DIMS = KT<KP>::DIMS;
+  const int ncl = nloc * plane;  // component stride of the low words (no ghost rows)
   // Only the shallow-water fluxes tell the two outer neighbours apart; the
   // other right-hand sides take their sum.
   constexpr bool kOrdered = KP == KP_SWE;
@@ -587,9 +588,9 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
       for (int q = 0; q < NC; ++q) {
         float w;
         if (euler) {
-          float l = ulo[q * ncell + cb + p];
+          float l = ulo[q * ncl + cb + p];
           two_sum_acc(uh[r][q][p], l, __fmul_rn(dt, k[q]));
-          ulo[q * ncell + cb + p] = l;
+          ulo[q * ncl + cb + p] = l;
           w = uh[r][q][p];
         } else if (STAGE == 0) {
           acc[r][q][p] = k[q];
@@ -602,9 +603,9 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
           w = uh[r][q][p] + dt * k[q];
         } else {
           const float a = acc[r][q][p] + k[q];
-          float l = ulo[q * ncell + cb + p];
+          float l = ulo[q * ncl + cb + p];
           two_sum_acc(uh[r][q][p], l, __fmul_rn(h6, a));
-          ulo[q * ncell + cb + p] = l;
+          ulo[q * ncl + cb + p] = l;
           w = uh[r][q][p];
         }
         wout[q][p] = w;
@@ -638,15 +639,16 @@ __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant_
   if (P.it.gate && !P.it.gate[item]) return; // uniform over the cluster
   const int plane = P.plane, nx = P.nx, ny = P.ny;
   const int nloc = P.outer / CS;
-  // shared memory: stage buffers 0/1 and the low words, each [NC][nloc + 2][plane]
-  // (outer rows -1 .. nloc; rows -1 and nloc of the stage buffers are the
-  // ghost rows), then two mbarriers
+  // shared memory: stage buffers 0/1, each [NC][nloc + 2][plane] (outer
+  // rows -1 .. nloc; rows -1 and nloc are the ghost rows), the low words
+  // [NC][nloc][plane], two mbarriers, the halo target table, abort flags
   const int ncell = (nloc + 2) * plane;
+  const int ncl = nloc * plane;
   float* const buf0 = reinterpret_cast<float*>(smem_raw) + plane;   // row 0 of buffer 0
   float* const buf1 = buf0 + NC * ncell;
-  float* const ulo = buf1 + NC * ncell;
+  float* const ulo = reinterpret_cast<float*>(smem_raw) + 2 * NC * ncell;
   uint64_t* const mbar = reinterpret_cast<uint64_t*>(
-      smem_raw + ((((size_t)3 * NC * ncell) * 4 + 15) & ~(size_t)15));
+      smem_raw + ((((size_t)2 * NC * ncell + (size_t)NC * ncl) * 4 + 15) & ~(size_t)15));
   const bool remote = DIMS >= 2 && CS > 1;
   const uint32_t sbase = cta_smem_u32(smem_raw);
   const uint32_t mb0 = cta_smem_u32(mbar);
@@ -724,7 +726,7 @@ __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant_
         uh[r][q][p] = h;
         acc[r][q][p] = 0.f;
         buf0[q * ncell + o * plane + rowoff + p] = h;
-        ulo[q * ncell + o * plane + rowoff + p] = (float)(v - (double)h);
+        ulo[q * ncl + o * plane + rowoff + p] = (float)(v - (double)h);
       }
   // every CTA's mbarriers and target table are initialised before anyone
   // pushes
@@ -815,7 +817,7 @@ __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant_
 #pragma unroll
       for (int p = 0; p < PX; ++p) {
         const int o = ofirst + dir * r;
-        const double v = (double)uh[r][q][p] + (double)ulo[q * ncell + o * plane + rowoff + p];
+        const double v = (double)uh[r][q][p] + (double)ulo[q * ncl + o * plane + rowoff + p];
         out[q * P.n + o * plane + rowoff + p] = v;
         if (out2) out2[q * P.n + o * plane + rowoff + p] = v;
       }
