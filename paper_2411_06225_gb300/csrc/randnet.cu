@@ -331,6 +331,7 @@ __device__ __forceinline__ void nn_partial_body(const T* q, const T* S, long lon
     const T* Sp = S + ((long long)b * cap + p) * d;
     T acc0 = T(0), acc1 = T(0);
     long long j = j0 + lane;
+#pragma unroll 4
     for (; j + 32 < j1; j += 64) {
       const T t0 = qb[j] - Sp[j];
       const T t1 = qb[j + 32] - Sp[j + 32];
@@ -547,23 +548,20 @@ __global__ void __launch_bounds__(256) k_topm_ridge(const TP* part, int nch,
   __shared__ double Lsh[RNP_MAX_M * RNP_MAX_M];
   __shared__ double rhs[RNP_MAX_M], ysh[RNP_MAX_M], xsh[RNP_MAX_M], lish[RNP_MAX_M];
   double* pq = phiq + (long long)b * phiq_bstride;
-  // query features (when their partials are given): the chunk partials in
-  // chunk order, + zeta, ReLU
-  if (fpart) {
-    for (int w = threadIdx.x; w < M; w += blockDim.x) {
-      const TP* fp = fpart + ((long long)b * M + w) * fnch;
-      TP acc = TP(0);
-      for (int k = 0; k < fnch; ++k) acc = acc + fp[k];
-      const double v = (double)acc + zeta[w];
-      pq[w] = v > 0.0 ? v : 0.0;
-    }
-  }
-  // distances: four interleaved partial sums over the chunks, then combined
+  // Distances first (their partial loads are issued before the feature
+  // partials', so both are in flight together): four interleaved partial
+  // sums over the chunks, then combined.  A thread keeps the keys of its
+  // first kKeys candidates (p = threadIdx.x + t * 256) in registers.
+  constexpr int kKeys = 4;
+  unsigned long long mykey[kKeys];
   double* db = dist + (long long)b * cap;
-  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+#pragma unroll
+  for (int t = 0; t < kKeys; ++t) mykey[t] = ~0ULL;
+  for (int p = threadIdx.x, t = 0; p < P; p += blockDim.x, ++t) {
     const TP* pp = part + ((long long)b * cap + p) * nch;
     TP a0 = TP(0), a1 = TP(0), a2 = TP(0), a3 = TP(0);
     int k = 0;
+#pragma unroll 8
     for (; k + 3 < nch; k += 4) {
       a0 = a0 + pp[k];
       a1 = a1 + pp[k + 1];
@@ -571,48 +569,110 @@ __global__ void __launch_bounds__(256) k_topm_ridge(const TP* part, int nch,
       a3 = a3 + pp[k + 3];
     }
     for (; k < nch; ++k) a0 = a0 + pp[k];
-    db[p] = (double)((a0 + a1) + (a2 + a3));
+    const double dv = (double)((a0 + a1) + (a2 + a3));
+    db[p] = dv;
+#pragma unroll
+    for (int u = 0; u < kKeys; ++u)
+      if (u == t) mykey[u] = (unsigned long long)__double_as_longlong(dv);
   }
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // m nearest: every warp selects its own me best among its candidates
-  // (p = warp * 32 + lane + k * 256), then warp 0 selects among those
-  for (int r = 0; r < me; ++r) {
-    unsigned long long bk = ~0ULL;
-    unsigned bi = 0xffffffffu;
-    for (int p = threadIdx.x; p < P; p += blockDim.x) {
-      bool taken = false;
-      for (int k = 0; k < r; ++k) taken |= (ci[warp * RNP_MAX_M + k] == (unsigned)p);
-      if (taken) continue;
-      const unsigned long long v = (unsigned long long)__double_as_longlong(db[p]);
-      if (v < bk || (v == bk && (unsigned)p < bi)) { bk = v; bi = (unsigned)p; }
+  // query features (when their partials are given): the chunk partials in
+  // chunk order, + zeta, ReLU
+  if (fpart) {
+    for (int w = threadIdx.x; w < M; w += blockDim.x) {
+      const TP* fp = fpart + ((long long)b * M + w) * fnch;
+      TP acc = TP(0);
+#pragma unroll 32
+      for (int k = 0; k < fnch; ++k) acc = acc + fp[k];
+      const double v = (double)acc + zeta[w];
+      pq[w] = v > 0.0 ? v : 0.0;
     }
-    unsigned long long wkey;
-    unsigned widx;
-    warp_min_key(bk, bi, &wkey, &widx);
-    if (lane == 0) { ck[warp * RNP_MAX_M + r] = wkey; ci[warp * RNP_MAX_M + r] = widx; }
-    __syncwarp();
   }
-  __syncthreads();
-  if (warp == 0) {
-    const int nc = kWarps * me;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (P <= kKeys * (int)blockDim.x) {
+    // m nearest with the keys in registers: each warp takes its me best
+    // (the winning lane drops its key), then warp 0 takes the me best of
+    // those
     for (int r = 0; r < me; ++r) {
       unsigned long long bk = ~0ULL;
       unsigned bi = 0xffffffffu;
-      for (int c = lane; c < nc; c += 32) {
-        const int w = c / me, k = c - w * me;
-        const unsigned long long v = ck[w * RNP_MAX_M + k];
-        const unsigned id = ci[w * RNP_MAX_M + k];
+      int bt = -1;
+#pragma unroll
+      for (int t = 0; t < kKeys; ++t) {
+        const unsigned p = (unsigned)(threadIdx.x + t * blockDim.x);
+        if (mykey[t] < bk || (mykey[t] == bk && mykey[t] != ~0ULL && p < bi)) {
+          bk = mykey[t]; bi = p; bt = t;
+        }
+      }
+      if (bk == ~0ULL) { bi = 0xffffffffu; bt = -1; }
+      unsigned long long wkey;
+      unsigned widx;
+      warp_min_key(bk, bi, &wkey, &widx);
+      if (bt >= 0 && bi == widx) {
+#pragma unroll
+        for (int t = 0; t < kKeys; ++t)
+          if (t == bt) mykey[t] = ~0ULL;
+      }
+      if (lane == 0) { ck[warp * RNP_MAX_M + r] = wkey; ci[warp * RNP_MAX_M + r] = widx; }
+    }
+  } else {
+    // more candidates than register slots: the same selection reading the
+    // distances back, with the warp's picks as the taken list
+    __syncthreads();
+    for (int r = 0; r < me; ++r) {
+      unsigned long long bk = ~0ULL;
+      unsigned bi = 0xffffffffu;
+      for (int p = threadIdx.x; p < P; p += blockDim.x) {
         bool taken = false;
-        for (int t = 0; t < r; ++t) taken |= (sel[t] == (int)id);
-        if (taken || id == 0xffffffffu) continue;
-        if (v < bk || (v == bk && id < bi)) { bk = v; bi = id; }
+        for (int k = 0; k < r; ++k) taken |= (ci[warp * RNP_MAX_M + k] == (unsigned)p);
+        if (taken) continue;
+        const unsigned long long v = (unsigned long long)__double_as_longlong(db[p]);
+        if (v < bk || (v == bk && (unsigned)p < bi)) { bk = v; bi = (unsigned)p; }
       }
       unsigned long long wkey;
       unsigned widx;
       warp_min_key(bk, bi, &wkey, &widx);
-      if (lane == 0) sel[r] = (int)widx;
+      if (lane == 0) { ck[warp * RNP_MAX_M + r] = wkey; ci[warp * RNP_MAX_M + r] = widx; }
       __syncwarp();
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    // the warps' picks, at most RNP_MAX_M per lane slot: lane c holds
+    // candidates c, c + 32, ... of the nw * me list; the winner drops its own
+    const int nc = kWarps * me;
+    unsigned long long lk[kWarps];
+    unsigned li2[kWarps];
+#pragma unroll
+    for (int t = 0; t < kWarps; ++t) {
+      const int c = lane + 32 * t;
+      if (c < nc) {
+        const int w = c / me, k = c - w * me;
+        lk[t] = ck[w * RNP_MAX_M + k];
+        li2[t] = ci[w * RNP_MAX_M + k];
+        if (li2[t] == 0xffffffffu) lk[t] = ~0ULL;
+      } else {
+        lk[t] = ~0ULL;
+        li2[t] = 0xffffffffu;
+      }
+    }
+    for (int r = 0; r < me; ++r) {
+      unsigned long long bk = ~0ULL;
+      unsigned bi = 0xffffffffu;
+      int bt = -1;
+#pragma unroll
+      for (int t = 0; t < kWarps; ++t)
+        if (lk[t] != ~0ULL && (lk[t] < bk || (lk[t] == bk && li2[t] < bi))) {
+          bk = lk[t]; bi = li2[t]; bt = t;
+        }
+      unsigned long long wkey;
+      unsigned widx;
+      warp_min_key(bk, bi, &wkey, &widx);
+      if (bt >= 0 && bi == widx) {
+#pragma unroll
+        for (int t = 0; t < kWarps; ++t)
+          if (t == bt) lk[t] = ~0ULL;
+      }
+      if (lane == 0) sel[r] = (int)widx;
     }
   }
   __syncthreads();
@@ -635,6 +695,7 @@ __global__ void __launch_bounds__(256) k_topm_ridge(const TP* part, int nch,
       xb = pq;
     }
     double acc = 0.0;
+#pragma unroll 4
     for (int w = lane; w < M; w += 32) acc = fma(xa[w], xb[w], acc);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -669,7 +730,13 @@ __global__ void __launch_bounds__(256) k_topm_ridge(const TP* part, int nch,
     return;
   }
   if (tries - 1 > 0) atomicAdd(esc_count, tries - 1);
-  for (int l = 0; l < me; ++l) alpha[b * RNP_MAX_M + l] = me <= 4 ? x[l] : xsh[l];
+  if (me <= 4) {
+#pragma unroll
+    for (int l = 0; l < 4; ++l)
+      if (l < me) alpha[b * RNP_MAX_M + l] = x[l];
+  } else {
+    for (int l = 0; l < me; ++l) alpha[b * RNP_MAX_M + l] = xsh[l];
+  }
 }
 
 template <typename TP>
