@@ -58,6 +58,23 @@ FLOPS_PER_CELL_UPDATE = {"diffreact2d": (4 * (16 + 12) + 2 * 13) / 2.0,
                          "burgers1d": 4 * 9 + 13.0}
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one fine launch
+# over all 64 slices of the diffusion-reaction workload, from the ncu capture
+# summarised in profiles/k_stencil_mixed_diffreact2d_128x128_N64.md; valid
+# only for the captured kernel and tiling, scaled by the slices a launch runs
+# (the kernel reads each start state once; results stay in L2).
+STENCIL_TRAFFIC = {"workload": "diffreact2d", "tiling": (8, 256, 2, 4),
+                   "bytes": 16857088, "slices": 64}
+
+
+def traffic_per_launch(tf: dict, slices: float):
+    t = STENCIL_TRAFFIC
+    if WORKLOAD != t["workload"] or \
+            (tf["cluster"], tf["threads"], tf["px"], tf["rs"]) != t["tiling"]:
+        return None
+    return t["bytes"] * slices / t["slices"]
+
+
 def peaks() -> dict:
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -340,6 +357,12 @@ def run_gpu(args):
         cells_per_launch = stats["fine_cell_updates"] / max(stats["K"], 1)
         achieved = cells_per_launch * flops_cu / (statistics.mean(fine_ms) / 1e3) / 1e12
         peak_alu = fp32_alu_peak_tflops(pk.get("sm_max_mhz", 2070.0))
+        tf = tiling["fine"]
+        kname = (f"k_stencil_mixed<{WORKLOAD}, PX={tf['px']}, RS={tf['rs']}> "
+                 f"cluster {tf['cluster']} x {tf['threads']} threads") if tf["px"] else \
+            f"k_stencil_fused<{WORKLOAD}, double> cluster {tf['cluster']}"
+        # slices per fine launch = cell-updates per launch / (nF steps x d unknowns)
+        traffic = traffic_per_launch(tf, cells_per_launch / (cfg["nF"] * W.dim(cfg)))
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup,
@@ -355,9 +378,9 @@ def run_gpu(args):
             "K": stats["K"], "fine_ms_per_iteration": statistics.mean(fine_ms),
             "stencil_tiling": tiling,
             "sweep_ms": stats["t_sweep_ms"], "fit_ms": stats["t_fit_ms"],
-            "roofline": {"kernel": "k_stencil_fused<DIFFREACT,float>", "bound": "alu",
+            "roofline": {"kernel": kname, "bound": "alu",
                          "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
-                         "frac": achieved / peak_alu, "traffic": None,
+                         "frac": achieved / peak_alu, "traffic": traffic,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock "
                                         f"{pk.get('sm_max_mhz', 2070.0)} MHz (MEASURED_PEAKS)"},
             "e2e": {"value": e2e_value, "unit": UNIT,
