@@ -112,6 +112,9 @@ def initial_condition(cfg: dict, seed: int | None = None,
       w ~ U(0.05,0.2), zero momentum.
     * ``sine``: single Fourier mode sin(2 pi k x / lx) (test operators), mode
       number cfg['mode'] (default 1), along each axis that has > 1 point.
+    * ``cos9``: u0(x) = 0.5 (cos(9 pi x / 2) + 1) on [-1, 1), the Burgers
+      initial condition of the paper's Burgers experiments (Sec. 5.1);
+      deterministic.
     """
     seed = cfg["seed"] if seed is None else seed
     batch = cfg.get("batch", 1) if batch is None else batch
@@ -146,6 +149,9 @@ def initial_condition(cfg: dict, seed: int | None = None,
             r2 = dy[:, None] ** 2 + dx[None, :] ** 2
             out[b, :n] = (1.0 + amp * np.exp(-r2 / (2.0 * w * w))).ravel()
             out[b, n:] = 0.0
+        elif kind == "cos9":
+            x = -1.0 + cfg["lx"] * np.arange(nx) / nx
+            out[b] = 0.5 * (np.cos(4.5 * np.pi * x) + 1.0)
         elif kind == "sine":
             k = cfg.get("mode", 1)
             x = np.arange(nx) / nx
