@@ -53,7 +53,7 @@ class Problem(C.Structure):
         ("N", C.c_int), ("nF", C.c_int), ("nG", C.c_int), ("M", C.c_int),
         ("m", C.c_int), ("lam", C.c_double), ("seed", C.c_uint64),
         ("tol", C.c_double), ("max_iters", C.c_int), ("corr", C.c_int),
-        ("scale_mode", C.c_int), ("gscheme", C.c_int),
+        ("scale_mode", C.c_int), ("gscheme", C.c_int), ("bc", C.c_int),
     ]
 
 
@@ -135,6 +135,7 @@ def problem(cfg: dict, **kw) -> Problem:
     p.corr = {"randnet": 0, "parareal": 1}[c.get("corr", "randnet")]
     p.scale_mode = {"minmax": 0, "none": 1}[c.get("scale", "minmax")]
     p.gscheme = {"euler": 0, "rk4": 1}[c.get("gscheme", "euler")]
+    p.bc = {"periodic": 0, "neumann": 1}[c.get("bc", "periodic")]
     return p
 
 

@@ -35,20 +35,29 @@ long orc_dim(const orc_problem* p) {
 
 /* Second difference along each axis, summed x + y + z:
  *   ((f[+1] - 2 f) + f[-1]) * (1 / h^2) per axis. */
+/* Index of the neighbour of cell i (0 <= i < n) in direction dir (+1/-1):
+ * periodic wrap, or -- no-flux wall -- the cell itself. */
+static int nbr(int i, int dir, int n, int bc) {
+  int j = i + dir;
+  if (j >= 0 && j < n) return j;
+  if (bc == ORC_BC_NEUMANN) return i;
+  return j < 0 ? j + n : j - n;
+}
+
 static double lap(const double* f, int x, int y, int z, int nx, int ny,
-                  int nz, int dims, double ix2, double iy2, double iz2) {
+                  int nz, int dims, double ix2, double iy2, double iz2, int bc) {
   long row = ((long)z * ny + y) * nx;
   double c = f[row + x];
-  double fe = f[row + (x + 1) % nx], fw = f[row + (x + nx - 1) % nx];
+  double fe = f[row + nbr(x, 1, nx, bc)], fw = f[row + nbr(x, -1, nx, bc)];
   double s = ((fe - 2.0 * c) + fw) * ix2;
   if (dims >= 2) {
-    double fn = f[((long)z * ny + (y + 1) % ny) * nx + x];
-    double fs = f[((long)z * ny + (y + ny - 1) % ny) * nx + x];
+    double fn = f[((long)z * ny + nbr(y, 1, ny, bc)) * nx + x];
+    double fs = f[((long)z * ny + nbr(y, -1, ny, bc)) * nx + x];
     s = s + ((fn - 2.0 * c) + fs) * iy2;
   }
   if (dims >= 3) {
-    double fu = f[((long)((z + 1) % nz) * ny + y) * nx + x];
-    double fd = f[((long)((z + nz - 1) % nz) * ny + y) * nx + x];
+    double fu = f[((long)nbr(z, 1, nz, bc) * ny + y) * nx + x];
+    double fd = f[((long)nbr(z, -1, nz, bc) * ny + y) * nx + x];
     s = s + ((fu - 2.0 * c) + fd) * iz2;
   }
   return s;
@@ -94,25 +103,25 @@ void orc_rhs(const orc_problem* p, const double* u, double* out) {
           case ORC_BURGERS1D: {
             /* nu * v_xx - v * v_x, central differences (Sec. 5.1). */
             double i2h = 0.5 / hx;
-            double v = u[i], ve = u[(x + 1) % nx], vw = u[(x + nx - 1) % nx];
-            double diff = P[0] * lap(u, x, 0, 0, nx, 1, 1, 1, ix2, 0, 0);
+            double v = u[i], ve = u[nbr(x, 1, nx, p->bc)], vw = u[nbr(x, -1, nx, p->bc)];
+            double diff = P[0] * lap(u, x, 0, 0, nx, 1, 1, 1, ix2, 0, 0, p->bc);
             out[i] = diff - v * ((ve - vw) * i2h);
           } break;
           case ORC_ADVECT1D: {
             double i2h = 0.5 / hx;
-            double ve = u[(x + 1) % nx], vw = u[(x + nx - 1) % nx];
+            double ve = u[nbr(x, 1, nx, p->bc)], vw = u[nbr(x, -1, nx, p->bc)];
             out[i] = -(P[0] * ((ve - vw) * i2h));
           } break;
           case ORC_HEAT: {
             int dims = nz > 1 ? 3 : (ny > 1 ? 2 : 1);
-            out[i] = P[0] * lap(u, x, y, z, nx, ny, nz, dims, ix2, iy2, iz2);
+            out[i] = P[0] * lap(u, x, y, z, nx, ny, nz, dims, ix2, iy2, iz2, p->bc);
           } break;
           case ORC_DIFFREACT2D: {
             /* Du lap u + (u - u^3 - c - v);  Dv lap v + (u - v)  (Sec. 5.2) */
             const double* uu = u; const double* vv = u + n;
             double a = uu[i], b = vv[i];
-            double lu = lap(uu, x, y, 0, nx, ny, 1, 2, ix2, iy2, 0);
-            double lv = lap(vv, x, y, 0, nx, ny, 1, 2, ix2, iy2, 0);
+            double lu = lap(uu, x, y, 0, nx, ny, 1, 2, ix2, iy2, 0, p->bc);
+            double lv = lap(vv, x, y, 0, nx, ny, 1, 2, ix2, iy2, 0, p->bc);
             out[i] = P[0] * lu + (((a - (a * a) * a) - P[2]) - b);
             out[n + i] = P[1] * lv + (a - b);
           } break;
@@ -121,8 +130,8 @@ void orc_rhs(const orc_problem* p, const double* u, double* out) {
             int dims = p->pde == ORC_BRUSS3D ? 3 : 2;
             const double* uu = u; const double* vv = u + n;
             double a = uu[i], b = vv[i];
-            double lu = lap(uu, x, y, z, nx, ny, nz, dims, ix2, iy2, iz2);
-            double lv = lap(vv, x, y, z, nx, ny, nz, dims, ix2, iy2, iz2);
+            double lu = lap(uu, x, y, z, nx, ny, nz, dims, ix2, iy2, iz2, p->bc);
+            double lv = lap(vv, x, y, z, nx, ny, nz, dims, ix2, iy2, iz2, p->bc);
             double a2 = a * a;
             double opb = 1.0 + P[1];
             out[i] = P[2] * lu + ((P[0] - opb * a) + b * a2);
@@ -460,7 +469,8 @@ int orc_solve(const orc_problem* p, const double* u0, double* U,
   const int N = p->N, M = p->M;
   const long d = orc_dim(p);
   if (N < 1 || p->nF < 1 || p->nG < 1 || p->m < 1 || p->m > 64 || M < 1 ||
-      p->max_iters < 1)
+      p->max_iters < 1 || p->bc < 0 || p->bc > 1 ||
+      (p->bc == ORC_BC_NEUMANN && p->pde == ORC_SWE2D))
     return ORC_EINVAL;
   const int K_max = p->max_iters < N ? p->max_iters : N;
   /* At most N - k + 1 pairs are appended at iteration k (L >= k - 1). */

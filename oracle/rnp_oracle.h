@@ -44,6 +44,11 @@ enum {
 };
 
 enum { ORC_CORR_RANDNET = 0, ORC_CORR_PARAREAL = 1 };
+/* Boundary: periodic, or no-flux (homogeneous Neumann) on a cell-centred
+ * finite-volume grid -- the flux through a wall face is zero, i.e. the
+ * neighbour across the wall is the cell itself (Sec. 5.2: no-flow
+ * Neumann boundary, finite-volume discretisation). */
+enum { ORC_BC_PERIODIC = 0, ORC_BC_NEUMANN = 1 };
 enum { ORC_SCALE_MINMAX = 0, ORC_SCALE_NONE = 1 };
 enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2, ORC_ENONFINITE = 4,
        ORC_ENOTCONV = 5 };
@@ -51,7 +56,7 @@ enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2, ORC_ENONFINITE = 4,
 typedef struct {
   int pde;
   int nx, ny, nz;           /* grid points per axis (ny = nz = 1 in 1D)   */
-  double lx, ly, lz;        /* periodic domain lengths                     */
+  double lx, ly, lz;        /* domain lengths (cell size lx / nx, ...)     */
   double param[8];          /* PDE coefficients, see orc_rhs               */
   double t0, tN;            /* time interval of Eq. 1                      */
   int N;                    /* number of time slices                       */
@@ -64,6 +69,7 @@ typedef struct {
   int corr;                 /* ORC_CORR_*                                  */
   int scale_mode;           /* ORC_SCALE_*                                 */
   int gscheme;              /* G integrator: 0 forward Euler (RK1), 1 RK4  */
+  int bc;                   /* ORC_BC_* (shallow water: periodic only)     */
 } orc_problem;
 
 typedef struct {
