@@ -57,9 +57,10 @@ typedef enum {
   RNP_EBUSY = 7        /* the server has no free slot                       */
 } rnp_status;
 
-/* h(u) of Eq. 1: periodic finite-difference semi-discretisations of the
- * paper's test systems (Sec. 5.1 Burgers, Sec. 5.2 diffusion-reaction,
- * App. E Brusselator, Sec. 5.3 shallow water) and two linear operators. */
+/* h(u) of Eq. 1: finite-difference semi-discretisations (periodic, or with
+ * no-flux walls, see rnp_bc) of the paper's test systems (Sec. 5.1 Burgers,
+ * Sec. 5.2 diffusion-reaction, App. E Brusselator, Sec. 5.3 shallow water)
+ * and two linear operators. */
 typedef enum {
   RNP_BURGERS1D = 0,   /* param: nu                                        */
   RNP_DIFFREACT2D = 1, /* param: Du, Dv, c   (FitzHugh-Nagumo kinetics)   */
@@ -94,6 +95,12 @@ typedef enum { RNP_SCALE_MINMAX = 0, RNP_SCALE_NONE = 1 } rnp_scale;
 
 typedef enum { RNP_G_EULER = 0, RNP_G_RK4 = 1 } rnp_gscheme;
 
+typedef enum { RNP_BC_PERIODIC = 0, RNP_BC_NEUMANN = 1 } rnp_bc;
+/* PERIODIC: every axis wraps.  NEUMANN: no-flux walls on a cell-centred
+ * finite-volume grid (Sec. 5.2's no-flow Neumann boundary): the flux through
+ * a wall face is zero, i.e. the neighbour across the wall is the cell
+ * itself.  Shallow water accepts PERIODIC only (RNP_EINVAL otherwise). */
+
 #define RNP_MAX_BATCH 64
 #define RNP_MAX_M 32   /* largest number of nearest neighbours m */
 
@@ -123,6 +130,7 @@ typedef struct {
   int autotune;           /* 1: rnp_create times every launchable stencil
                              tiling on the context's buffers and keeps the
                              fastest (ignored when cluster/threads are set) */
+  int bc;                 /* rnp_bc                                        */
 } rnp_problem;
 
 typedef struct {

@@ -166,6 +166,9 @@ const char* validate(const rnp_problem* p) {
   if (p->max_iters < 1) return "max_iters must be >= 1";
   if (p->batch < 1 || p->batch > RNP_MAX_BATCH) return "batch must be in [1, 64]";
   if (p->corr != RNP_CORR_RANDNET && p->corr != RNP_CORR_PARAREAL) return "unknown corr";
+  if (p->bc != RNP_BC_PERIODIC && p->bc != RNP_BC_NEUMANN) return "unknown bc";
+  if (p->bc == RNP_BC_NEUMANN && p->pde == RNP_SWE2D)
+    return "shallow water supports periodic boundaries only";
   if (p->scale_mode != RNP_SCALE_MINMAX && p->scale_mode != RNP_SCALE_NONE)
     return "unknown scale_mode";
   if (p->gscheme != RNP_G_EULER && p->gscheme != RNP_G_RK4) return "unknown gscheme";

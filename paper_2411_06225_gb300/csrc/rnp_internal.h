@@ -35,6 +35,7 @@ struct Geom {
   long long d;     // ncomp * n
   int outer;       // extent of the axis split across a cluster (x/y/z for 1/2/3D)
   long long plane; // cells per outer index
+  int bc;          // rnp_bc: 0 periodic, 1 no-flux walls (wall neighbour = the cell)
 };
 
 // PDE constants, precomputed on the host in FP64 exactly as the plain

@@ -78,6 +78,7 @@ Geom make_geom(const rnp_problem& p) {
   if (g.dims == 1) { g.outer = 1; g.plane = p.nx; }
   else if (g.dims == 2) { g.outer = p.ny; g.plane = p.nx; }
   else { g.outer = p.nz; g.plane = (long long)p.nx * p.ny; }
+  g.bc = p.bc;
   return g;
 }
 
@@ -125,17 +126,17 @@ static bool x_shuffles(const Geom& g, int PX) {
   return w >= 1 && w <= 32 && (32 % w) == 0;
 }
 
-static FusedFn mixed_fn(int kp, int PX, int RS, bool XS) {
+static FusedFn mixed_fn(int kp, int PX, int RS, bool XS, bool WALL) {
   switch (kp) {
-    case KP_BURGERS: return mixed_fn_burgers(PX, RS, XS);
-    case KP_ADVECT: return mixed_fn_advect(PX, RS, XS);
-    case KP_HEAT1: return mixed_fn_heat1(PX, RS, XS);
-    case KP_HEAT2: return mixed_fn_heat2(PX, RS, XS);
-    case KP_HEAT3: return mixed_fn_heat3(PX, RS, XS);
-    case KP_DIFFREACT: return mixed_fn_diffreact(PX, RS, XS);
-    case KP_BRUSS2: return mixed_fn_bruss2(PX, RS, XS);
-    case KP_BRUSS3: return mixed_fn_bruss3(PX, RS, XS);
-    case KP_SWE: return mixed_fn_swe(PX, RS, XS);
+    case KP_BURGERS: return mixed_fn_burgers(PX, RS, XS, WALL);
+    case KP_ADVECT: return mixed_fn_advect(PX, RS, XS, WALL);
+    case KP_HEAT1: return mixed_fn_heat1(PX, RS, XS, WALL);
+    case KP_HEAT2: return mixed_fn_heat2(PX, RS, XS, WALL);
+    case KP_HEAT3: return mixed_fn_heat3(PX, RS, XS, WALL);
+    case KP_DIFFREACT: return mixed_fn_diffreact(PX, RS, XS, WALL);
+    case KP_BRUSS2: return mixed_fn_bruss2(PX, RS, XS, WALL);
+    case KP_BRUSS3: return mixed_fn_bruss3(PX, RS, XS, WALL);
+    case KP_SWE: return mixed_fn_swe(PX, RS, XS, WALL);
   }
   return nullptr;
 }
@@ -230,7 +231,7 @@ static bool try_cfg(const Geom& g, bool fp32, int CS, int threads, int nitems,
         const long long t = tiles * (nloc / RS);
         if (t > 512 || t < 1) continue;
         if (threads > 0 && t != threads) continue;
-        FusedFn fn = mixed_fn(g.kp, PX, RS, x_shuffles(g, PX));
+        FusedFn fn = mixed_fn(g.kp, PX, RS, x_shuffles(g, PX), g.bc != 0);
         if (!fn || !launchable(fn, CS, (int)t, smem, nitems)) continue;
         out->cluster = CS;
         out->threads = (int)t;
@@ -360,7 +361,7 @@ cudaError_t launch_stencil_fused(const Geom& g, const Coef& c, bool fp32, int sc
   if (it.n <= 0 || steps <= 0) return cudaSuccess;
   // a mixed-precision context uses the FP64 kernel where no FP32 tile fits
   const bool use_mixed = fp32 && cfg.px > 0;
-  FusedFn fn = use_mixed ? mixed_fn(g.kp, cfg.px, cfg.rs, x_shuffles(g, cfg.px))
+  FusedFn fn = use_mixed ? mixed_fn(g.kp, cfg.px, cfg.rs, x_shuffles(g, cfg.px), g.bc != 0)
                          : fused_fn(g.kp, false, cfg.R);
   if (!fn) return cudaErrorInvalidValue;
   FusedParams P;
@@ -373,6 +374,7 @@ cudaError_t launch_stencil_fused(const Geom& g, const Coef& c, bool fp32, int sc
   for (int i = 0; i < 12; ++i) P.kf[i] = (float)c.k[i];
   P.fdt = (float)P.dt; P.fh2 = (float)P.h2; P.fh6 = (float)P.h6;
   P.err = err;
+  P.bc = g.bc;
   cudaLaunchConfig_t lc = {};
   cudaLaunchAttribute at[1];
   lc.gridDim = dim3(cfg.cluster * it.n);
@@ -427,6 +429,7 @@ cudaError_t launch_stencil_plain(const Geom& g, const Coef& c, int scheme, int s
   P.U = U; P.Acc = Acc; P.gate = it.gate; P.nitems = it.n;
   P.nx = g.nx; P.ny = g.ny; P.nz = g.nz; P.n = g.n; P.d = g.d;
   P.scheme = scheme; P.dt = dt; P.h2 = dt / 2.0; P.h6 = dt / 6.0; P.coef = c;
+  P.bc = g.bc;
   const int S = scheme == SCHEME_RK4 ? 4 : 1;
   const long long cells = (long long)it.n * g.n;
   int cur = 0;

@@ -149,6 +149,7 @@ struct FusedParams {
   float kf[12];      // coefficients rounded to FP32 (mixed kernel)
   float fdt, fh2, fh6;
   int* err;          // set to 1 when a halo wait times out (mixed kernel)
+  int bc;            // 0 periodic, 1 no-flux walls (the wall neighbour is the cell)
 };
 
 template <int KP, typename T, bool EX, int R>
@@ -216,8 +217,10 @@ __global__ void __launch_bounds__(512, 1) k_stencil_fused(const FusedParams P) {
         const int ii = c - o * plane;
         int x, y;
         if (DIMS == 3) { y = ii / nx; x = ii - y * nx; } else { x = ii; y = 0; }
-        const int xe = (x + 1 == nx) ? 0 : x + 1;
-        const int xw = (x == 0) ? nx - 1 : x - 1;
+        // neighbours: periodic wrap, or the cell itself across a no-flux wall
+        const bool wall = P.bc != 0;
+        const int xe = (x + 1 == nx) ? (wall ? x : 0) : x + 1;
+        const int xw = (x == 0) ? (wall ? 0 : nx - 1) : x - 1;
         const int rowb = o * plane + (DIMS == 3 ? y * nx : 0);
         T Cv[NC], Ev[NC], Wv[NC], Nv[NC], Sv[NC], Uv[NC], Dv[NC];
 #pragma unroll
@@ -228,17 +231,20 @@ __global__ void __launch_bounds__(512, 1) k_stencil_fused(const FusedParams P) {
           Wv[q] = Bq[rowb + xw];
           Nv[q] = Sv[q] = Uv[q] = Dv[q] = T(0);
           if (DIMS == 3) {
-            const int yn = (y + 1 == ny) ? 0 : y + 1;
-            const int ys = (y == 0) ? ny - 1 : y - 1;
+            const int yn = (y + 1 == ny) ? (wall ? y : 0) : y + 1;
+            const int ys = (y == 0) ? (wall ? 0 : ny - 1) : y - 1;
             Nv[q] = Bq[o * plane + yn * nx + x];
             Sv[q] = Bq[o * plane + ys * nx + x];
           }
           if (DIMS >= 2) {
-            // outer neighbours: local, or the neighbouring CTA's first/last plane
+            // outer neighbours: local, the neighbouring CTA's first/last
+            // plane, or (at a wall) the cell itself
             T vp, vm;
             if (o + 1 < nloc) vp = Bq[c + plane];
+            else if (wall && rank == CS - 1) vp = Cv[q];
             else vp = BN[q * ncell + ii];
             if (o > 0) vm = Bq[c - plane];
+            else if (wall && rank == 0) vm = Cv[q];
             else vm = BP[q * ncell + (nloc - 1) * plane + ii];
             if (DIMS == 2) { Nv[q] = vp; Sv[q] = vm; } else { Uv[q] = vp; Dv[q] = vm; }
           }
@@ -302,6 +308,7 @@ struct PlainParams {
   int stage, scheme;
   double dt, h2, h6;
   Coef coef;
+  int bc;             // 0 periodic, 1 no-flux walls
 };
 
 template <int KP>
@@ -318,9 +325,14 @@ __global__ void k_stage_plain(const PlainParams P) {
     const int x = (int)(cell % nx);
     const int y = (int)((cell / nx) % ny);
     const int z = (int)(cell / ((long long)nx * ny));
-    const int xe = (x + 1) % nx, xw = (x + nx - 1) % nx;
-    const int yn = (y + 1) % ny, ys = (y + ny - 1) % ny;
-    const int zu = (z + 1) % nz, zd = (z + nz - 1) % nz;
+    // neighbours: periodic wrap, or the cell itself across a no-flux wall
+    const bool wall = P.bc != 0;
+    const int xe = x + 1 < nx ? x + 1 : (wall ? x : 0);
+    const int xw = x > 0 ? x - 1 : (wall ? x : nx - 1);
+    const int yn = y + 1 < ny ? y + 1 : (wall ? y : 0);
+    const int ys = y > 0 ? y - 1 : (wall ? y : ny - 1);
+    const int zu = z + 1 < nz ? z + 1 : (wall ? z : 0);
+    const int zd = z > 0 ? z - 1 : (wall ? z : nz - 1);
     auto at = [&](int xx, int yy, int zz) { return ((long long)zz * ny + yy) * nx + xx; };
     const double* W = P.Wc + (long long)item * P.d;
     double Cv[NC], Ev[NC], Wv[NC], Nv[NC], Sv[NC], Uv[NC], Dv[NC];
@@ -471,7 +483,9 @@ __device__ __forceinline__ bool halo_wait(uint32_t mbar, uint32_t parity) {
 
 // Where a stage sends its edge rows: outer row 0 to the previous rank's
 // ghost row nloc, outer row nloc - 1 to the next rank's ghost row -1, both
-// in the buffer of the next stage's parity.  Addresses are 32-bit
+// in the buffer of the next stage's parity (with no-flux walls the first and
+// last ranks keep their wall rows: row 0 to their own ghost row -1, row
+// nloc - 1 to their own ghost row nloc).  Addresses are 32-bit
 // shared-window addresses: the neighbours' windows (mapa) for a cluster of
 // several CTAs, this CTA's own window for a one-CTA cluster (periodic wrap
 // onto itself, written with plain shared stores).  The four targets are the
@@ -505,11 +519,12 @@ __device__ __forceinline__ void push_edge(const HaloOut& h, bool to_prev, uint32
                                           const float* v) {
   const uint4 t = *h.tab;
   const uint32_t a = (to_prev ? t.x : t.y) + h.boff + 4u * elem;
-  if (h.self) st_shared_vec<PX>(a, v);
-  else st_async_vec<PX>(a, v, (to_prev ? t.z : t.w) + h.moff);
+  const uint32_t mb = to_prev ? t.z : t.w;  // 0: a local target (wall)
+  if (h.self || mb == 0) st_shared_vec<PX>(a, v);
+  else st_async_vec<PX>(a, v, mb + h.moff);
 }
 
-template <int KP, int PX, int RS, int STAGE, bool XS>
+template <int KP, int PX, int RS, int STAGE, bool XS, bool WALL>
 __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* __restrict__ B,
                                             float* __restrict__ Bn, float* ulo,
                                             float (&uh)[RS][KT<KP>::NC][PX],
@@ -517,7 +532,7 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
                                             int ncell, int plane, int nloc, int ofirst, int dir,
                                             int rowoff, int woff, int eoff, int yn_off, int ys_off,
                                             bool euler, const HaloOut& ho, unsigned xmask,
-                                            int xw, int xwest, int xeast) {
+                                            int xw, int xwest, int xeast, bool xlo, bool xhi) {
   const float* kk = P.kf;
   const float dt = P.fdt, h2 = P.fh2, h6 = P.fh6;
   constexpr int NC = KT<KP>::NC, DIMS = KT<KP>::DIMS;
@@ -561,6 +576,11 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
         ld_vec<PX>(Bq + eoff, ve);
         ew[q] = vw[PX - 1];
         ee[q] = ve[0];
+      }
+      if constexpr (WALL) {
+        // no-flux walls: the neighbour across the wall is the cell itself
+        if (xlo) ew[q] = cur[q][0];
+        if (xhi) ee[q] = cur[q][PX - 1];
       }
       if (DIMS == 3) {
         ld_vec<PX>(Bq + yn_off, yn[q]);
@@ -628,7 +648,7 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
   }
 }
 
-template <int KP, int PX, int RS, bool XS>
+template <int KP, int PX, int RS, bool XS, bool WALL>
 __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant__ FusedParams P) {
   constexpr int NC = KT<KP>::NC, DIMS = KT<KP>::DIMS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -666,10 +686,15 @@ __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant_
   const int yrow = rowoff / nx;                // y index in 3D (0 otherwise)
   const int xw = x0 == 0 ? nx - 1 : x0 - 1;
   const int xe = x0 + PX == nx ? 0 : x0 + PX;
-  const int yn_off = (DIMS == 3 ? ((yrow + 1 == ny ? 0 : yrow + 1) * nx) : 0) + x0;
-  const int ys_off = (DIMS == 3 ? ((yrow == 0 ? ny - 1 : yrow - 1) * nx) : 0) + x0;
-  // first cells of the tiles west and east of this one (periodic in x)
+  // y neighbours inside a 3D plane: periodic, or the row itself at a wall
+  const int yn_row = yrow + 1 == ny ? (WALL ? yrow : 0) : yrow + 1;
+  const int ys_row = yrow == 0 ? (WALL ? 0 : ny - 1) : yrow - 1;
+  const int yn_off = (DIMS == 3 ? yn_row * nx : 0) + x0;
+  const int ys_off = (DIMS == 3 ? ys_row * nx : 0) + x0;
+  // first cells of the tiles west and east of this one (periodic in x; at a
+  // wall the value is replaced by the cell's own)
   const int woff = yrow * nx + (xw + 1 - PX), eoff = yrow * nx + xe;
+  const bool xlo = WALL && x0 == 0, xhi = WALL && x0 + PX == nx;
   const bool first = o0 == 0, last = o0 + RS == nloc;
   const bool edge = DIMS >= 2 && (first || last);
   // the group owning the last row (unless it also owns the first) walks
@@ -689,6 +714,10 @@ __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant_
   // last row the next rank's ghost row -1 (buffer 0; +boff for buffer 1)
   uint4* const tab = reinterpret_cast<uint4*>(mbar + 2);
   volatile int* const abort_flag = reinterpret_cast<volatile int*>(tab + 1);  // [2]
+  // With no-flux walls the first rank's row 0 fills its own S ghost row and
+  // the last rank's last row its own N ghost row (local stores, no mbarrier:
+  // a zero mbarrier address in the table marks a local target).
+  const bool wall_lo = WALL && rank == 0, wall_hi = WALL && rank == CS - 1;
   if (threadIdx.x == 0) {
     abort_flag[0] = abort_flag[1] = 0;
     uint32_t rb_prev = sbase, rb_next = sbase;
@@ -696,8 +725,11 @@ __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant_
       rb_prev = cluster_map_u32(sbase, (rank + CS - 1) % CS);
       rb_next = cluster_map_u32(sbase, (rank + 1) % CS);
     }
-    *tab = make_uint4(rb_prev + (uint32_t)((nloc + 1) * plane) * 4u, rb_next,
-                      rb_prev + (mb0 - sbase), rb_next + (mb0 - sbase));
+    const uint32_t ghostN = (uint32_t)((nloc + 1) * plane) * 4u, mboff = mb0 - sbase;
+    uint4 t = make_uint4(rb_prev + ghostN, rb_next, rb_prev + mboff, rb_next + mboff);
+    if (wall_lo) { t.x = sbase; t.z = 0; }
+    if (wall_hi) { t.y = sbase + ghostN; t.w = 0; }
+    *tab = t;
   }
   auto halo_out = [&](int par, bool on) {
     HaloOut h;
@@ -709,7 +741,9 @@ __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant_
     h.moff = 8u * par;
     return h;
   };
-  const uint32_t tx_bytes = (uint32_t)(2 * NC * plane * 4);
+  // ghost rows that arrive from other CTAs each stage
+  const int n_remote = remote ? (wall_lo ? 0 : 1) + (wall_hi ? 0 : 1) : 0;
+  const uint32_t tx_bytes = (uint32_t)(n_remote * NC * plane * 4);
 
   const long long base = (long long)rank * nloc * plane;
   const double* in = P.in + item_off(P.it.src_off, P.it.src_base, P.it.src_stride, item) + base;
@@ -774,9 +808,10 @@ __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant_
     return abort_flag[s & 1] != 0;
   };
 #define RNP_MIXED_STAGE(STG, BIN, BOUT, PAR, ON, EUL)                                          \
-  mixed_stage<KP, PX, RS, STG, XS>(P, BIN, BOUT, ulo, uh, acc, ncell, plane, nloc, ofirst,    \
-                                   dir, rowoff, woff, eoff, yn_off, ys_off, EUL,             \
-                                   halo_out((PAR) ^ 1, ON), xmask, xsw, xwest, xeast)
+  mixed_stage<KP, PX, RS, STG, XS, WALL>(P, BIN, BOUT, ulo, uh, acc, ncell, plane, nloc,      \
+                                         ofirst, dir, rowoff, woff, eoff, yn_off, ys_off,    \
+                                         EUL, halo_out((PAR) ^ 1, ON), xmask, xsw, xwest,    \
+                                         xeast, xlo, xhi)
 
   __syncthreads();
   for (int step = 0; step < P.steps; ++step) {
@@ -842,35 +877,43 @@ inline FusedFn fused_for_R(int R) {
 // beyond use and are not instantiated (the host picker never asks for them).
 static constexpr int kMaxTileValues = 40;
 
-template <int KP, int PX, int RS, bool XS>
+// Shallow water has periodic boundaries only: no wall instantiations.
+template <int KP, int PX, int RS, bool XS, bool WALL>
 inline FusedFn mixed_if_fits() {
-  if constexpr (RS * KT<KP>::NC * PX <= kMaxTileValues) return k_stencil_mixed<KP, PX, RS, XS>;
-  else return nullptr;
+  if constexpr (RS * KT<KP>::NC * PX <= kMaxTileValues && !(WALL && KP == KP_SWE))
+    return k_stencil_mixed<KP, PX, RS, XS, WALL>;
+  else
+    return nullptr;
 }
 
-template <int KP, int PX, bool XS>
+template <int KP, int PX, bool XS, bool WALL>
 inline FusedFn mixed_for_RS(int RS) {
   switch (RS) {
-    case 1: return mixed_if_fits<KP, PX, 1, XS>();
-    case 2: return mixed_if_fits<KP, PX, 2, XS>();
-    case 4: return mixed_if_fits<KP, PX, 4, XS>();
-    case 5: return mixed_if_fits<KP, PX, 5, XS>();
-    case 8: return mixed_if_fits<KP, PX, 8, XS>();
+    case 1: return mixed_if_fits<KP, PX, 1, XS, WALL>();
+    case 2: return mixed_if_fits<KP, PX, 2, XS, WALL>();
+    case 4: return mixed_if_fits<KP, PX, 4, XS, WALL>();
+    case 5: return mixed_if_fits<KP, PX, 5, XS, WALL>();
+    case 8: return mixed_if_fits<KP, PX, 8, XS, WALL>();
     default: return nullptr;
   }
 }
 
+template <int KP, int PX, bool WALL>
+inline FusedFn mixed_for_xs(int RS, bool XS) {
+  return XS ? mixed_for_RS<KP, PX, true, WALL>(RS) : mixed_for_RS<KP, PX, false, WALL>(RS);
+}
+
 template <int KP>
-inline FusedFn mixed_for(int PX, int RS, bool XS) {
-  if (PX == 2) return XS ? mixed_for_RS<KP, 2, true>(RS) : mixed_for_RS<KP, 2, false>(RS);
-  if (PX == 4) return XS ? mixed_for_RS<KP, 4, true>(RS) : mixed_for_RS<KP, 4, false>(RS);
+inline FusedFn mixed_for(int PX, int RS, bool XS, bool WALL) {
+  if (PX == 2) return WALL ? mixed_for_xs<KP, 2, true>(RS, XS) : mixed_for_xs<KP, 2, false>(RS, XS);
+  if (PX == 4) return WALL ? mixed_for_xs<KP, 4, true>(RS, XS) : mixed_for_xs<KP, 4, false>(RS, XS);
   return nullptr;
 }
 
 // Per-PDE entry points, defined in stencil_<pde>.cu.
 #define RNP_STENCIL_DECL(NAME)                 \
   FusedFn fused_fn_##NAME(bool fp32, int R);   \
-  FusedFn mixed_fn_##NAME(int PX, int RS, bool XS); \
+  FusedFn mixed_fn_##NAME(int PX, int RS, bool XS, bool WALL); \
   PlainFn plain_fn_##NAME();
 RNP_STENCIL_DECL(burgers)
 RNP_STENCIL_DECL(advect)
@@ -887,7 +930,9 @@ RNP_STENCIL_DECL(swe)
   FusedFn fused_fn_##NAME(bool fp32, int R) {                                        \
     return fp32 ? fused_for_R<KPV, float, false>(R) : fused_for_R<KPV, double, true>(R); \
   }                                                                                  \
-  FusedFn mixed_fn_##NAME(int PX, int RS, bool XS) { return mixed_for<KPV>(PX, RS, XS); } \
+  FusedFn mixed_fn_##NAME(int PX, int RS, bool XS, bool WALL) {                      \
+    return mixed_for<KPV>(PX, RS, XS, WALL);                                         \
+  }                                                                                  \
   PlainFn plain_fn_##NAME() { return k_stage_plain<KPV>; }
 
 }  // namespace rnp
