@@ -1,0 +1,101 @@
+"""Edge cases of the CUDA path against the FP64 oracle: the largest batch
+(64 members in one context), the largest neighbour count (m = 32), a single
+time slice (N = 1: the solve is F itself), and a ragged odd grid."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    import paper_2411_06225_gb300 as rnp
+    rnp.build()
+    rnp.lib()
+    return rnp
+
+
+def dev(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def test_largest_batch_matches_oracle_per_member(R, orc):
+    # nu = 0.05 keeps every one of the 64 random initial states resolved on
+    # 32 points (with nu = 0.01 some steepen into shocks the grid cannot hold)
+    cfg = W.config("burgers1d", nx=32, N=8, nF=40, nG=8, m=2, param=[0.05],
+                   batch=R.MAX_BATCH)
+    u0 = W.initial_condition(cfg)
+    p = orc.problem(cfg)
+    with R.Solver(R.problem(cfg, precision="fp64")) as s:
+        U, st = s.solve(dev(u0))
+        U = host(U)
+    for b in range(R.MAX_BATCH):
+        rc, Uo, so, _ = orc.solve(p, u0[b])
+        assert rc == 0
+        assert st["K_each"][b] == so.K
+        assert rel(U[b], Uo) < 1e-10, b
+
+
+def test_largest_m_predict_matches_oracle(R, orc):
+    cfg = W.config("diffreact2d", nx=16, ny=12, M=48, m=R.MAX_M)
+    p = orc.problem(cfg)
+    d = W.dim(cfg)
+    P = 45
+    rng = np.random.default_rng(9)
+    Uin = rng.standard_normal((1, P, d))
+    Y = rng.standard_normal((1, P, d))
+    q = Uin[:, 7] + 0.05 * rng.standard_normal((1, d))
+    c = np.array([[0.1, -0.2, 0.0]])
+    r = np.array([[1.5, 2.5, 1.0]])
+    A, z = orc.weights(p)
+    with R.Solver(R.problem(cfg, max_pairs=P)) as s:
+        s.set_scaling(c, r)
+        s.randnet_fit(dev(Uin), dev(Y))
+        out = host(s.randnet_predict(dev(q)))[0]
+    S = np.stack([orc.scale(p, c[0], r[0], u) for u in Uin[0]])
+    Phi = np.stack([orc.features(A, z, sr) for sr in S])
+    rc, ref, nn = orc.predict(p, S, Y[0], Phi, A, z, c[0], r[0], q[0])
+    assert rc >= 0
+    assert rel(out, ref) < 1e-9
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_single_slice_solve_is_the_fine_solver(R, orc, precision):
+    cfg = W.config("diffreact2d", nx=32, ny=32, N=1, nF=60, tN=0.1)
+    u0 = W.initial_condition(cfg)
+    with R.Solver(R.problem(cfg, precision=precision)) as s:
+        U, st = s.solve(dev(u0))
+        U = host(U)[0]
+    ref = orc.fine(orc.problem(cfg), u0[0])
+    assert st["K"] == 1 and st["converged"]
+    assert np.array_equal(U[0], u0[0])
+    if precision == "fp64":
+        assert np.array_equal(U[1], ref)
+    else:
+        assert rel(U[1], ref) <= 2e-7
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_odd_grid_solve(R, orc, precision):
+    # 19 x 19 x 2 has no FP32 tile (x-points per thread must divide 19):
+    # the mixed context runs the FP64 stencil there and still matches
+    cfg = W.config("diffreact2d", nx=19, ny=19, N=8, nF=100, nG=4, tN=1.0)
+    u0 = W.initial_condition(cfg)
+    orc.set_threads(8)
+    rc, Uo, so, _ = orc.solve(orc.problem(cfg), u0[0])
+    with R.Solver(R.problem(cfg, precision=precision)) as s:
+        U, st = s.solve(dev(u0))
+        U = host(U)[0]
+    assert abs(st["K"] - so.K) <= (0 if precision == "fp64" else 1)
+    assert rel(U, Uo) <= (1e-10 if precision == "fp64" else 1e-5)
