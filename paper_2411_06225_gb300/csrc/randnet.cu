@@ -201,7 +201,10 @@ static const int kFeatFW = 16;
 
 int features_chunks(long long d) { return (int)((d + kFeatCH - 1) / kFeatCH); }
 
-template <typename T, typename TP>
+// Partials of row r, neuron w, chunk ch at part[(r * M + w) * nch + ch]
+// (row-major, CM = false) or at part[(ch * R + r) * M + w] (chunk-major: the
+// finishing threads, one per neuron, then read consecutive addresses).
+template <typename T, typename TP, bool CM>
 __device__ __forceinline__ void feat_partial_body(T (&sS)[kFeatTR][kFeatCH], const T* A, int M,
                                                   long long d, const T* S, Rows rows, int R,
                                                   TP* part, int nch, const int* gate,
@@ -243,7 +246,11 @@ __device__ __forceinline__ void feat_partial_body(T (&sS)[kFeatTR][kFeatCH], con
     if (lane == 0) {
 #pragma unroll
       for (int r = 0; r < kFeatTR; ++r)
-        if (r0 + r < R) part[((long long)(r0 + r) * M + w) * nch + ch] = (TP)acc[r];
+        if (r0 + r < R) {
+          const long long at = CM ? ((long long)ch * R + (r0 + r)) * M + w
+                                  : ((long long)(r0 + r) * M + w) * nch + ch;
+          part[at] = (TP)acc[r];
+        }
     }
   }
 }
@@ -254,8 +261,8 @@ __global__ void __launch_bounds__(256) k_feat_partial(const T* A, int M, long lo
                                                       double* part, int nch,
                                                       const int* gate) {
   __shared__ T sS[kFeatTR][kFeatCH];
-  feat_partial_body<T, double>(sS, A, M, d, S, rows, R, part, nch, gate, blockIdx.x, blockIdx.y,
-                               blockIdx.z);
+  feat_partial_body<T, double, false>(sS, A, M, d, S, rows, R, part, nch, gate, blockIdx.x,
+                                      blockIdx.y, blockIdx.z);
 }
 
 __global__ void k_feat_finish(const double* part, int nch, int R, int M, const double* zeta,
@@ -315,11 +322,14 @@ static long long nn_chunk_len(long long d) {
 
 int nn_chunks(long long d) { return (int)((d + nn_chunk_len(d) - 1) / nn_chunk_len(d)); }
 
+// Partial of member b, stored row p, chunk ch at part[(ch * B + b) * cap + p]
+// (chunk-major: the finishing threads, one per stored row, read consecutive
+// addresses).
 template <typename T>
 __device__ __forceinline__ void nn_partial_body(const T* q, const T* S, long long cap,
                                                 long long d, long long chl, const int* P,
                                                 T* part, int nch, const int* gate,
-                                                int ch, int by, int gy, int b) {
+                                                int ch, int by, int gy, int b, int B) {
   if (gate && !gate[b]) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int Pb = P[b];
@@ -345,7 +355,7 @@ __device__ __forceinline__ void nn_partial_body(const T* q, const T* S, long lon
     T acc = acc0 + acc1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) part[((long long)b * cap + p) * nch + ch] = acc;
+    if (lane == 0) part[((long long)ch * B + b) * cap + p] = acc;
   }
 }
 
@@ -355,7 +365,7 @@ __global__ void __launch_bounds__(256) k_nn_partial(const T* q, const T* S, long
                                                     const int* P, T* part, int nch,
                                                     const int* gate) {
   nn_partial_body<T>(q, S, cap, d, chl, P, part, nch, gate, blockIdx.x, blockIdx.y, gridDim.y,
-                     blockIdx.z);
+                     blockIdx.z, gridDim.z);
 }
 
 // One launch for both halves of a RandNet query: blocks [0, nfb) compute the
@@ -370,13 +380,13 @@ __global__ void __launch_bounds__(256) k_query_partials(
   int bid = blockIdx.x;
   if (bid < nfb) {
     const int ch = bid % fnch, rest = bid / fnch;
-    feat_partial_body<T, T>(sS, A, M, d, q, qrows, R, fpart, fnch, gate, ch, rest % nry,
-                            rest / nry);
+    feat_partial_body<T, T, true>(sS, A, M, d, q, qrows, R, fpart, fnch, gate, ch, rest % nry,
+                                  rest / nry);
     return;
   }
   bid -= nfb;
   const int ch = bid % nnch, rest = bid / nnch;
-  nn_partial_body<T>(q, S, cap, d, chl, P, npart, nnch, gate, ch, rest % gy, gy, rest / gy);
+  nn_partial_body<T>(q, S, cap, d, chl, P, npart, nnch, gate, ch, rest % gy, gy, rest / gy, R);
 }
 
 template <typename T>
@@ -557,18 +567,20 @@ __global__ void __launch_bounds__(256) k_topm_ridge(const TP* part, int nch,
   double* db = dist + (long long)b * cap;
 #pragma unroll
   for (int t = 0; t < kKeys; ++t) mykey[t] = ~0ULL;
+  const int B = gridDim.x;                          // members (one CTA each)
+  const long long cstride = (long long)B * cap;     // chunk k of row p at pp[k * cstride]
   for (int p = threadIdx.x, t = 0; p < P; p += blockDim.x, ++t) {
-    const TP* pp = part + ((long long)b * cap + p) * nch;
+    const TP* pp = part + (long long)b * cap + p;
     TP a0 = TP(0), a1 = TP(0), a2 = TP(0), a3 = TP(0);
     int k = 0;
-#pragma unroll 8
+#pragma unroll 4
     for (; k + 3 < nch; k += 4) {
-      a0 = a0 + pp[k];
-      a1 = a1 + pp[k + 1];
-      a2 = a2 + pp[k + 2];
-      a3 = a3 + pp[k + 3];
+      a0 = a0 + pp[k * cstride];
+      a1 = a1 + pp[(k + 1) * cstride];
+      a2 = a2 + pp[(k + 2) * cstride];
+      a3 = a3 + pp[(k + 3) * cstride];
     }
-    for (; k < nch; ++k) a0 = a0 + pp[k];
+    for (; k < nch; ++k) a0 = a0 + pp[k * cstride];
     const double dv = (double)((a0 + a1) + (a2 + a3));
     db[p] = dv;
 #pragma unroll
@@ -579,10 +591,10 @@ __global__ void __launch_bounds__(256) k_topm_ridge(const TP* part, int nch,
   // chunk order, + zeta, ReLU
   if (fpart) {
     for (int w = threadIdx.x; w < M; w += blockDim.x) {
-      const TP* fp = fpart + ((long long)b * M + w) * fnch;
+      const TP* fp = fpart + (long long)b * M + w;   // chunk k at fp[k * B * M]
       TP acc = TP(0);
-#pragma unroll 32
-      for (int k = 0; k < fnch; ++k) acc = acc + fp[k];
+#pragma unroll 16
+      for (int k = 0; k < fnch; ++k) acc = acc + fp[(long long)k * B * M];
       const double v = (double)acc + zeta[w];
       pq[w] = v > 0.0 ? v : 0.0;
     }
