@@ -227,10 +227,11 @@ __device__ __forceinline__ void feat_partial_body(T (&sS)[kFeatTR][kFeatCH], con
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int w = w0 + warp; w < M && w < w0 + kFeatFW; w += 8) {
     const T* Aw = A + (long long)w * d + j0;
+    // (loops unrolled so that a lane's loads of a chunk are in flight together)
     T acc[kFeatTR];
 #pragma unroll
     for (int r = 0; r < kFeatTR; ++r) acc[r] = T(0);
-#pragma unroll 4
+#pragma unroll 16
     for (int j = lane; j < len; j += 32) {
       const T a = Aw[j];
 #pragma unroll
@@ -341,7 +342,7 @@ __device__ __forceinline__ void nn_partial_body(const T* q, const T* S, long lon
     const T* Sp = S + ((long long)b * cap + p) * d;
     T acc0 = T(0), acc1 = T(0);
     long long j = j0 + lane;
-#pragma unroll 4
+#pragma unroll 16
     for (; j + 32 < j1; j += 64) {
       const T t0 = qb[j] - Sp[j];
       const T t1 = qb[j + 32] - Sp[j + 32];
