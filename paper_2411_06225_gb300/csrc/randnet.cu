@@ -427,8 +427,28 @@ static cudaError_t launch_query_t(const T* A, int M, long long d, const T* q, in
   const int nry = (B + kFeatTR - 1) / kFeatTR, nwz = (M + kFeatFW - 1) / kFeatFW;
   const int nfb = fnch * nry * nwz;
   const int nnch = nn_chunks(d);
+  // distance blocks: enough that the whole query fits one wave of resident
+  // blocks (rows are strided, so fewer blocks each take more rows); the
+  // grid does not depend on the dataset size, so a captured graph stays valid
+  static int slots[2] = {0, 0};   // resident blocks on the device, per T
+  int& sl = slots[sizeof(T) == 8 ? 1 : 0];
+  if (sl == 0) {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_query_partials<T>, 256, 0) ==
+            cudaSuccess)
+      sl = sms * per;
+    else
+      sl = -1;
+    cudaGetLastError();
+  }
   int gy = (Pmax + kNnRows - 1) / kNnRows;
   if (gy > 32) gy = 32;
+  if (sl > 0) {
+    const int fit = (sl - nfb) / (nnch * B);
+    if (fit >= 1 && fit < gy) gy = fit;
+  }
   if (Pmax <= 0) gy = 0;
   const long long nblocks = (long long)nfb + (long long)nnch * gy * B;
   count_launches(1);
