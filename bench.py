@@ -59,20 +59,21 @@ FLOPS_PER_CELL_UPDATE = {"diffreact2d": (4 * (16 + 12) + 2 * 13) / 2.0,
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one fine launch
-# over all 64 slices of the diffusion-reaction workload, from the ncu capture
-# summarised in profiles/k_stencil_mixed_diffreact2d_128x128_N64.md; valid
-# only for the captured kernel and tiling, scaled by the slices a launch runs
-# (the kernel reads each start state once; results stay in L2).
-STENCIL_TRAFFIC = {"workload": "diffreact2d", "tiling": (8, 256, 2, 4),
-                   "bytes": 16857088, "slices": 64}
+# over all 64 slices of the diffusion-reaction workload, per tiling (cluster,
+# threads, PX, RS), from the ncu captures summarised in
+# profiles/k_stencil_mixed_diffreact2d_128x128_N64.md; valid only for the
+# captured kernels, scaled by the slices a launch runs (the kernel reads each
+# start state once; its results stay in L2).
+STENCIL_TRAFFIC = {"workload": "diffreact2d", "slices": 64,
+                   "bytes": {(8, 256, 2, 4): 16888320, (16, 128, 2, 4): 16884224}}
 
 
 def traffic_per_launch(tf: dict, slices: float):
     t = STENCIL_TRAFFIC
-    if WORKLOAD != t["workload"] or \
-            (tf["cluster"], tf["threads"], tf["px"], tf["rs"]) != t["tiling"]:
+    key = (tf["cluster"], tf["threads"], tf["px"], tf["rs"])
+    if WORKLOAD != t["workload"] or key not in t["bytes"]:
         return None
-    return t["bytes"] * slices / t["slices"]
+    return t["bytes"][key] * slices / t["slices"]
 
 
 def peaks() -> dict:
