@@ -104,17 +104,18 @@ Coef make_coef(const rnp_problem& p, const Geom& g) {
   return c;
 }
 
-static FusedFn fused_fn(int kp, bool fp32, int R) {
+// The FP64 fused kernel (every operation explicitly rounded).
+static FusedFn fused_fn(int kp, int R) {
   switch (kp) {
-    case KP_BURGERS: return fused_fn_burgers(fp32, R);
-    case KP_ADVECT: return fused_fn_advect(fp32, R);
-    case KP_HEAT1: return fused_fn_heat1(fp32, R);
-    case KP_HEAT2: return fused_fn_heat2(fp32, R);
-    case KP_HEAT3: return fused_fn_heat3(fp32, R);
-    case KP_DIFFREACT: return fused_fn_diffreact(fp32, R);
-    case KP_BRUSS2: return fused_fn_bruss2(fp32, R);
-    case KP_BRUSS3: return fused_fn_bruss3(fp32, R);
-    case KP_SWE: return fused_fn_swe(fp32, R);
+    case KP_BURGERS: return fused_fn_burgers(R);
+    case KP_ADVECT: return fused_fn_advect(R);
+    case KP_HEAT1: return fused_fn_heat1(R);
+    case KP_HEAT2: return fused_fn_heat2(R);
+    case KP_HEAT3: return fused_fn_heat3(R);
+    case KP_DIFFREACT: return fused_fn_diffreact(R);
+    case KP_BRUSS2: return fused_fn_bruss2(R);
+    case KP_BRUSS3: return fused_fn_bruss3(R);
+    case KP_SWE: return fused_fn_swe(R);
   }
   return nullptr;
 }
@@ -255,7 +256,7 @@ static bool try_cfg(const Geom& g, bool fp32, int CS, int threads, int nitems,
   }
   const int R = round_R((ncell + threads - 1) / threads);
   if (R < 0) return false;
-  FusedFn fn = fused_fn(g.kp, false, R);
+  FusedFn fn = fused_fn(g.kp, R);
   if (!fn || !launchable(fn, CS, threads, smem_bytes(g, false, CS), nitems)) return false;
   out->cluster = CS;
   out->threads = threads;
@@ -362,7 +363,7 @@ cudaError_t launch_stencil_fused(const Geom& g, const Coef& c, bool fp32, int sc
   // a mixed-precision context uses the FP64 kernel where no FP32 tile fits
   const bool use_mixed = fp32 && cfg.px > 0;
   FusedFn fn = use_mixed ? mixed_fn(g.kp, cfg.px, cfg.rs, x_shuffles(g, cfg.px), g.bc != 0)
-                         : fused_fn(g.kp, false, cfg.R);
+                         : fused_fn(g.kp, cfg.R);
   if (!fn) return cudaErrorInvalidValue;
   FusedParams P;
   P.in = in; P.out = out; P.out2 = out2;

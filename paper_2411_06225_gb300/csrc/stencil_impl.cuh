@@ -912,7 +912,7 @@ inline FusedFn mixed_for(int PX, int RS, bool XS, bool WALL) {
 
 // Per-PDE entry points, defined in stencil_<pde>.cu.
 #define RNP_STENCIL_DECL(NAME)                 \
-  FusedFn fused_fn_##NAME(bool fp32, int R);   \
+  FusedFn fused_fn_##NAME(int R);              \
   FusedFn mixed_fn_##NAME(int PX, int RS, bool XS, bool WALL); \
   PlainFn plain_fn_##NAME();
 RNP_STENCIL_DECL(burgers)
@@ -927,9 +927,7 @@ RNP_STENCIL_DECL(swe)
 #undef RNP_STENCIL_DECL
 
 #define RNP_STENCIL_DEFINE(KPV, NAME)                                                \
-  FusedFn fused_fn_##NAME(bool fp32, int R) {                                        \
-    return fp32 ? fused_for_R<KPV, float, false>(R) : fused_for_R<KPV, double, true>(R); \
-  }                                                                                  \
+  FusedFn fused_fn_##NAME(int R) { return fused_for_R<KPV, double, true>(R); }       \
   FusedFn mixed_fn_##NAME(int PX, int RS, bool XS, bool WALL) {                      \
     return mixed_for<KPV>(PX, RS, XS, WALL);                                         \
   }                                                                                  \
