@@ -31,7 +31,10 @@ static const int kTcM = 128;      // rows per tile (tcgen05 M)
 static const int kTcN = 128;      // neurons per tile (tcgen05 N); M <= 128
 static const int kTcKB = 64;      // K elements per shared-memory block (128 B of BF16)
 static const int kTcChunk = 256;  // K elements per CTA (split-K chunk)
-static const long long kSpinLimit = 1LL << 20;
+// Bound of a wait on the MMA-commit mbarrier: kPolls polls of at most
+// kPollNs suspension each.
+static const unsigned kPollNs = 1000;
+static const unsigned kPolls = 2u << 20;
 
 int features_tc_chunks(long long d) { return (int)((d + kTcChunk - 1) / kTcChunk); }
 
@@ -69,15 +72,18 @@ __device__ __forceinline__ uint32_t sw128_offset(int r, int k) {
   return (uint32_t)(r * 128 + ((chunk ^ (r & 7)) << 4) + ((k * 2) & 15));
 }
 
+// Polls until the phase completes; every poll may suspend the thread for at
+// most kPollNs (the suspend-time hint), so kPolls polls bound the wait at
+// about 2 s.  Returns false when the wait gave up.
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (long long it = 0; it < kSpinLimit; ++it) {
+  for (unsigned it = 0; it < kPolls; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n"
-        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
-        : "r"(mbar), "r"(parity)
+        : "r"(mbar), "r"(parity), "r"(kPollNs)
         : "memory");
     if (done) return true;
   }

@@ -434,7 +434,11 @@ __device__ __forceinline__ void two_sum_acc(float& uh, float& ul, float x) {
 }
 
 // --- distributed-shared-memory halo exchange ------------------------------
-static constexpr long long kHaloSpin = 1LL << 24;  // try_wait polls before a wait gives up
+// Bound of a halo wait: kPolls polls (each may suspend the thread for the
+// hardware's own short time limit; a suspend-time hint would cost the
+// register-tight stencil a spill).
+static constexpr unsigned kPolls = 2u << 20;
+
 
 __device__ __forceinline__ uint32_t cta_smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -466,8 +470,10 @@ __device__ __forceinline__ void mbar_expect(uint32_t mbar, uint32_t bytes) {
 }
 // Bounded wait for the phase of the given parity; acquire at cluster scope
 // (the bytes were written by other CTAs of the cluster).
+// Polls until the phase completes, at most kPolls times; false when the
+// wait gave up.
 __device__ __forceinline__ bool halo_wait(uint32_t mbar, uint32_t parity) {
-  for (long long it = 0; it < kHaloSpin; ++it) {
+  for (unsigned it = 0; it < kPolls; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n"
