@@ -376,6 +376,9 @@ cudaError_t launch_stencil_fused(const Geom& g, const Coef& c, bool fp32, int sc
   P.fdt = (float)P.dt; P.fh2 = (float)P.h2; P.fh6 = (float)P.h6;
   P.err = err;
   P.bc = g.bc;
+  P.nloc = g.outer / cfg.cluster;
+  P.mcell = (P.nloc + 2) * (int)g.plane;
+  P.mcl = P.nloc * (int)g.plane;
   cudaLaunchConfig_t lc = {};
   cudaLaunchAttribute at[1];
   lc.gridDim = dim3(cfg.cluster * it.n);

@@ -150,6 +150,10 @@ struct FusedParams {
   float fdt, fh2, fh6;
   int* err;          // set to 1 when a halo wait times out (mixed kernel)
   int bc;            // 0 periodic, 1 no-flux walls (the wall neighbour is the cell)
+  // mixed kernel, per launch: outer rows per CTA and the component strides
+  // of its stage buffers (with ghost rows) and low words, read from the
+  // parameter space instead of being kept in registers
+  int nloc, mcell, mcl;
 };
 
 template <int KP, typename T, bool EX, int R>
@@ -542,7 +546,7 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
   const float* kk = P.kf;
   const float dt = P.fdt, h2 = P.fh2, h6 = P.fh6;
   constexpr int NC = KT<KP>::NC, DIMS = KT<KP>::DIMS;
-  const int ncl = nloc * plane;  // component stride of the low words (no ghost rows)
+  const int ncl = P.mcl;  // component stride of the low words (no ghost rows)
   // Only the shallow-water fluxes tell the two outer neighbours apart; the
   // other right-hand sides take their sum.
   constexpr bool kOrdered = KP == KP_SWE;
@@ -664,12 +668,12 @@ __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant_
   if (item >= P.it.n) return;                // uniform over the cluster
   if (P.it.gate && !P.it.gate[item]) return; // uniform over the cluster
   const int plane = P.plane, nx = P.nx, ny = P.ny;
-  const int nloc = P.outer / CS;
+  const int nloc = P.nloc;
   // shared memory: stage buffers 0/1, each [NC][nloc + 2][plane] (outer
   // rows -1 .. nloc; rows -1 and nloc are the ghost rows), the low words
   // [NC][nloc][plane], two mbarriers, the halo target table, abort flags
-  const int ncell = (nloc + 2) * plane;
-  const int ncl = nloc * plane;
+  const int ncell = P.mcell;   // (nloc + 2) * plane
+  const int ncl = P.mcl;       // nloc * plane
   float* const buf0 = reinterpret_cast<float*>(smem_raw) + plane;   // row 0 of buffer 0
   float* const buf1 = buf0 + NC * ncell;
   float* const ulo = reinterpret_cast<float*>(smem_raw) + 2 * NC * ncell;
