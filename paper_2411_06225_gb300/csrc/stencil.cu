@@ -379,6 +379,8 @@ cudaError_t launch_stencil_fused(const Geom& g, const Coef& c, bool fp32, int sc
   P.nloc = g.outer / cfg.cluster;
   P.mcell = (P.nloc + 2) * (int)g.plane;
   P.mcl = P.nloc * (int)g.plane;
+  P.moff = (int)((((size_t)2 * g.ncomp * P.mcell + (size_t)g.ncomp * P.mcl) * 4 + 15) &
+                 ~(size_t)15);
   cudaLaunchConfig_t lc = {};
   cudaLaunchAttribute at[1];
   lc.gridDim = dim3(cfg.cluster * it.n);

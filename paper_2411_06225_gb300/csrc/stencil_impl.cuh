@@ -154,6 +154,7 @@ struct FusedParams {
   // of its stage buffers (with ghost rows) and low words, read from the
   // parameter space instead of being kept in registers
   int nloc, mcell, mcl;
+  int moff;          // byte offset of the mbarriers in the dynamic shared memory
 };
 
 template <int KP, typename T, bool EX, int R>
@@ -677,8 +678,8 @@ __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant_
   float* const buf0 = reinterpret_cast<float*>(smem_raw) + plane;   // row 0 of buffer 0
   float* const buf1 = buf0 + NC * ncell;
   float* const ulo = reinterpret_cast<float*>(smem_raw) + 2 * NC * ncell;
-  uint64_t* const mbar = reinterpret_cast<uint64_t*>(
-      smem_raw + ((((size_t)2 * NC * ncell + (size_t)NC * ncl) * 4 + 15) & ~(size_t)15));
+  // (P.moff = the 16-byte aligned end of the buffers: 4 (2 NC ncell + NC ncl))
+  uint64_t* const mbar = reinterpret_cast<uint64_t*>(smem_raw + P.moff);
   const bool remote = DIMS >= 2 && CS > 1;
   const uint32_t sbase = cta_smem_u32(smem_raw);
   const uint32_t mb0 = cta_smem_u32(mbar);
