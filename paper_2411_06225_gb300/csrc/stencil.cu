@@ -127,17 +127,17 @@ static bool x_shuffles(const Geom& g, int PX) {
   return w >= 1 && w <= 32 && (32 % w) == 0;
 }
 
-static FusedFn mixed_fn(int kp, int PX, int RS, bool XS, bool WALL) {
+static FusedFn mixed_fn(int kp, int PX, int RS, bool XS, bool WALL, bool RK) {
   switch (kp) {
-    case KP_BURGERS: return mixed_fn_burgers(PX, RS, XS, WALL);
-    case KP_ADVECT: return mixed_fn_advect(PX, RS, XS, WALL);
-    case KP_HEAT1: return mixed_fn_heat1(PX, RS, XS, WALL);
-    case KP_HEAT2: return mixed_fn_heat2(PX, RS, XS, WALL);
-    case KP_HEAT3: return mixed_fn_heat3(PX, RS, XS, WALL);
-    case KP_DIFFREACT: return mixed_fn_diffreact(PX, RS, XS, WALL);
-    case KP_BRUSS2: return mixed_fn_bruss2(PX, RS, XS, WALL);
-    case KP_BRUSS3: return mixed_fn_bruss3(PX, RS, XS, WALL);
-    case KP_SWE: return mixed_fn_swe(PX, RS, XS, WALL);
+    case KP_BURGERS: return mixed_fn_burgers(PX, RS, XS, WALL, RK);
+    case KP_ADVECT: return mixed_fn_advect(PX, RS, XS, WALL, RK);
+    case KP_HEAT1: return mixed_fn_heat1(PX, RS, XS, WALL, RK);
+    case KP_HEAT2: return mixed_fn_heat2(PX, RS, XS, WALL, RK);
+    case KP_HEAT3: return mixed_fn_heat3(PX, RS, XS, WALL, RK);
+    case KP_DIFFREACT: return mixed_fn_diffreact(PX, RS, XS, WALL, RK);
+    case KP_BRUSS2: return mixed_fn_bruss2(PX, RS, XS, WALL, RK);
+    case KP_BRUSS3: return mixed_fn_bruss3(PX, RS, XS, WALL, RK);
+    case KP_SWE: return mixed_fn_swe(PX, RS, XS, WALL, RK);
   }
   return nullptr;
 }
@@ -232,8 +232,13 @@ static bool try_cfg(const Geom& g, bool fp32, int CS, int threads, int nitems,
         const long long t = tiles * (nloc / RS);
         if (t > 512 || t < 1) continue;
         if (threads > 0 && t != threads) continue;
-        FusedFn fn = mixed_fn(g.kp, PX, RS, x_shuffles(g, PX), g.bc != 0);
-        if (!fn || !launchable(fn, CS, (int)t, smem, nitems)) continue;
+        // the RK4 and the Euler instantiation of this tile (the RK4 one is
+        // the larger: it decides launchability)
+        FusedFn fn = mixed_fn(g.kp, PX, RS, x_shuffles(g, PX), g.bc != 0, true);
+        FusedFn fe = mixed_fn(g.kp, PX, RS, x_shuffles(g, PX), g.bc != 0, false);
+        if (!fn || !fe || !launchable(fn, CS, (int)t, smem, nitems) ||
+            !launchable(fe, CS, (int)t, smem, nitems))
+          continue;
         out->cluster = CS;
         out->threads = (int)t;
         out->R = 0;
@@ -362,7 +367,8 @@ cudaError_t launch_stencil_fused(const Geom& g, const Coef& c, bool fp32, int sc
   if (it.n <= 0 || steps <= 0) return cudaSuccess;
   // a mixed-precision context uses the FP64 kernel where no FP32 tile fits
   const bool use_mixed = fp32 && cfg.px > 0;
-  FusedFn fn = use_mixed ? mixed_fn(g.kp, cfg.px, cfg.rs, x_shuffles(g, cfg.px), g.bc != 0)
+  FusedFn fn = use_mixed ? mixed_fn(g.kp, cfg.px, cfg.rs, x_shuffles(g, cfg.px), g.bc != 0,
+                                    scheme == SCHEME_RK4)
                          : fused_fn(g.kp, cfg.R);
   if (!fn) return cudaErrorInvalidValue;
   FusedParams P;

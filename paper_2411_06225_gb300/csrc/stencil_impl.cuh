@@ -659,7 +659,9 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
   }
 }
 
-template <int KP, int PX, int RS, bool XS, bool WALL>
+// RK: the fine solver's RK4 (true) or the coarse forward Euler (false), one
+// instantiation each, so the RK4 kernel carries no Euler code (registers).
+template <int KP, int PX, int RS, bool XS, bool WALL, bool RK>
 __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant__ FusedParams P) {
   constexpr int NC = KT<KP>::NC, DIMS = KT<KP>::DIMS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -800,8 +802,7 @@ __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant_
   // threads that read ghost rows (those owning an edge row) wait for its
   // phase, parity (s >> 1) & 1, with cluster-scope acquire; the other warps
   // start computing at once.
-  const bool rk4 = P.scheme == SCHEME_RK4;
-  const int nst = rk4 ? 4 * P.steps : P.steps;
+  const int nst = RK ? 4 * P.steps : P.steps;
   auto stage_begin = [&](int s) {
     if (!remote) return;
     if (threadIdx.x == 0) mbar_expect(mb0 + 8u * (s & 1), tx_bytes);
@@ -826,7 +827,7 @@ __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant_
 
   __syncthreads();
   for (int step = 0; step < P.steps; ++step) {
-    if (rk4) {
+    if constexpr (RK) {
       const int s0 = 4 * step;
       stage_begin(s0);
       RNP_MIXED_STAGE(0, buf0, buf1, 0, true, false);
@@ -889,42 +890,47 @@ inline FusedFn fused_for_R(int R) {
 static constexpr int kMaxTileValues = 40;
 
 // Shallow water has periodic boundaries only: no wall instantiations.
-template <int KP, int PX, int RS, bool XS, bool WALL>
+template <int KP, int PX, int RS, bool XS, bool WALL, bool RK>
 inline FusedFn mixed_if_fits() {
   if constexpr (RS * KT<KP>::NC * PX <= kMaxTileValues && !(WALL && KP == KP_SWE))
-    return k_stencil_mixed<KP, PX, RS, XS, WALL>;
+    return k_stencil_mixed<KP, PX, RS, XS, WALL, RK>;
   else
     return nullptr;
 }
 
-template <int KP, int PX, bool XS, bool WALL>
+template <int KP, int PX, bool XS, bool WALL, bool RK>
 inline FusedFn mixed_for_RS(int RS) {
   switch (RS) {
-    case 1: return mixed_if_fits<KP, PX, 1, XS, WALL>();
-    case 2: return mixed_if_fits<KP, PX, 2, XS, WALL>();
-    case 4: return mixed_if_fits<KP, PX, 4, XS, WALL>();
-    case 5: return mixed_if_fits<KP, PX, 5, XS, WALL>();
-    case 8: return mixed_if_fits<KP, PX, 8, XS, WALL>();
+    case 1: return mixed_if_fits<KP, PX, 1, XS, WALL, RK>();
+    case 2: return mixed_if_fits<KP, PX, 2, XS, WALL, RK>();
+    case 4: return mixed_if_fits<KP, PX, 4, XS, WALL, RK>();
+    case 5: return mixed_if_fits<KP, PX, 5, XS, WALL, RK>();
+    case 8: return mixed_if_fits<KP, PX, 8, XS, WALL, RK>();
     default: return nullptr;
   }
 }
 
-template <int KP, int PX, bool WALL>
+template <int KP, int PX, bool WALL, bool RK>
 inline FusedFn mixed_for_xs(int RS, bool XS) {
-  return XS ? mixed_for_RS<KP, PX, true, WALL>(RS) : mixed_for_RS<KP, PX, false, WALL>(RS);
+  return XS ? mixed_for_RS<KP, PX, true, WALL, RK>(RS) : mixed_for_RS<KP, PX, false, WALL, RK>(RS);
+}
+
+template <int KP, int PX, bool RK>
+inline FusedFn mixed_for_wall(int RS, bool XS, bool WALL) {
+  return WALL ? mixed_for_xs<KP, PX, true, RK>(RS, XS) : mixed_for_xs<KP, PX, false, RK>(RS, XS);
 }
 
 template <int KP>
-inline FusedFn mixed_for(int PX, int RS, bool XS, bool WALL) {
-  if (PX == 2) return WALL ? mixed_for_xs<KP, 2, true>(RS, XS) : mixed_for_xs<KP, 2, false>(RS, XS);
-  if (PX == 4) return WALL ? mixed_for_xs<KP, 4, true>(RS, XS) : mixed_for_xs<KP, 4, false>(RS, XS);
+inline FusedFn mixed_for(int PX, int RS, bool XS, bool WALL, bool RK) {
+  if (PX == 2) return RK ? mixed_for_wall<KP, 2, true>(RS, XS, WALL) : mixed_for_wall<KP, 2, false>(RS, XS, WALL);
+  if (PX == 4) return RK ? mixed_for_wall<KP, 4, true>(RS, XS, WALL) : mixed_for_wall<KP, 4, false>(RS, XS, WALL);
   return nullptr;
 }
 
 // Per-PDE entry points, defined in stencil_<pde>.cu.
 #define RNP_STENCIL_DECL(NAME)                 \
   FusedFn fused_fn_##NAME(int R);              \
-  FusedFn mixed_fn_##NAME(int PX, int RS, bool XS, bool WALL); \
+  FusedFn mixed_fn_##NAME(int PX, int RS, bool XS, bool WALL, bool RK); \
   PlainFn plain_fn_##NAME();
 RNP_STENCIL_DECL(burgers)
 RNP_STENCIL_DECL(advect)
@@ -939,8 +945,8 @@ RNP_STENCIL_DECL(swe)
 
 #define RNP_STENCIL_DEFINE(KPV, NAME)                                                \
   FusedFn fused_fn_##NAME(int R) { return fused_for_R<KPV, double, true>(R); }       \
-  FusedFn mixed_fn_##NAME(int PX, int RS, bool XS, bool WALL) {                      \
-    return mixed_for<KPV>(PX, RS, XS, WALL);                                         \
+  FusedFn mixed_fn_##NAME(int PX, int RS, bool XS, bool WALL, bool RK) {             \
+    return mixed_for<KPV>(PX, RS, XS, WALL, RK);                                     \
   }                                                                                  \
   PlainFn plain_fn_##NAME() { return k_stage_plain<KPV>; }
 
