@@ -54,6 +54,7 @@ class Problem(C.Structure):
         ("m", C.c_int), ("lam", C.c_double), ("seed", C.c_uint64),
         ("tol", C.c_double), ("max_iters", C.c_int), ("corr", C.c_int),
         ("scale_mode", C.c_int), ("gscheme", C.c_int), ("bc", C.c_int),
+        ("fscheme", C.c_int),
     ]
 
 
@@ -85,6 +86,8 @@ def lib():
             "orc_rhs": (None, [P, _DP, _DP]),
             "orc_rk4": (None, [P, _DP, C.c_double, C.c_int]),
             "orc_euler": (None, [P, _DP, C.c_double, C.c_int]),
+            "orc_rk8": (None, [P, _DP, C.c_double, C.c_int]),
+            "orc_rk8_tableau": (None, [_DP, _DP, _DP]),
             "orc_fine": (None, [P, _DP, _DP]),
             "orc_coarse": (None, [P, _DP, _DP]),
             "orc_serial_fine": (None, [P, _DP, _DP]),
@@ -136,6 +139,7 @@ def problem(cfg: dict, **kw) -> Problem:
     p.scale_mode = {"minmax": 0, "none": 1}[c.get("scale", "minmax")]
     p.gscheme = {"euler": 0, "rk4": 1}[c.get("gscheme", "euler")]
     p.bc = {"periodic": 0, "neumann": 1}[c.get("bc", "periodic")]
+    p.fscheme = {"rk4": 0, "rk8": 1}[c.get("fscheme", "rk4")]
     return p
 
 
@@ -158,6 +162,23 @@ def rk4(p: Problem, u: np.ndarray, dt: float, n: int) -> np.ndarray:
     v = np.array(u, np.float64, copy=True)
     lib().orc_rk4(C.byref(p), _dp(v), dt, n)
     return v
+
+
+def rk8(p: Problem, u: np.ndarray, dt: float, n: int) -> np.ndarray:
+    v = np.array(u, np.float64, copy=True)
+    lib().orc_rk8(C.byref(p), _dp(v), dt, n)
+    return v
+
+
+def rk8_tableau():
+    """(A, b, c) of the oracle's RK8 as an 11 x 11 strictly lower-triangular
+    matrix and two vectors."""
+    a, b, c = np.zeros(55), np.zeros(11), np.zeros(11)
+    lib().orc_rk8_tableau(_dp(a), _dp(b), _dp(c))
+    A = np.zeros((11, 11))
+    for s in range(1, 11):
+        A[s, :s] = a[s * (s - 1) // 2: s * (s - 1) // 2 + s]
+    return A, b, c
 
 
 def euler(p: Problem, u: np.ndarray, dt: float, n: int) -> np.ndarray:

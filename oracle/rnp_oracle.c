@@ -188,6 +188,95 @@ void orc_rk4(const orc_problem* p, double* u, double dt, int nsteps) {
   free(w); free(k); free(acc);
 }
 
+/* Cooper & Verner's eighth-order explicit Runge-Kutta method with eleven
+ * stages (SIAM J. Numer. Anal. 9, 1972), written out from its published
+ * tableau; every entry is a rational number or a rational combination of
+ * sqrt(21).  Rows s = 1..10 of the strictly lower-triangular A are stored
+ * contiguously: a_{s,j} at a[s*(s-1)/2 + j]. */
+void orc_rk8_tableau(double* a, double* b, double* c) {
+  const double r = sqrt(21.0);
+  double A[11][11];
+  memset(A, 0, sizeof(A));
+  A[1][0] = 1.0 / 2.0;
+  A[2][0] = 1.0 / 4.0;
+  A[2][1] = 1.0 / 4.0;
+  A[3][0] = 1.0 / 7.0;
+  A[3][1] = (-7.0 - 3.0 * r) / 98.0;
+  A[3][2] = (21.0 + 5.0 * r) / 49.0;
+  A[4][0] = (11.0 + r) / 84.0;
+  A[4][2] = (18.0 + 4.0 * r) / 63.0;
+  A[4][3] = (21.0 - r) / 252.0;
+  A[5][0] = (5.0 + r) / 48.0;
+  A[5][2] = (9.0 + r) / 36.0;
+  A[5][3] = (-231.0 + 14.0 * r) / 360.0;
+  A[5][4] = (63.0 - 7.0 * r) / 80.0;
+  A[6][0] = (10.0 - r) / 42.0;
+  A[6][2] = (-432.0 + 92.0 * r) / 315.0;
+  A[6][3] = (633.0 - 145.0 * r) / 90.0;
+  A[6][4] = (-504.0 + 115.0 * r) / 70.0;
+  A[6][5] = (63.0 - 13.0 * r) / 35.0;
+  A[7][0] = 1.0 / 14.0;
+  A[7][4] = (14.0 - 3.0 * r) / 126.0;
+  A[7][5] = (13.0 - 3.0 * r) / 63.0;
+  A[7][6] = 1.0 / 9.0;
+  A[8][0] = 1.0 / 32.0;
+  A[8][4] = (91.0 - 21.0 * r) / 576.0;
+  A[8][5] = 11.0 / 72.0;
+  A[8][6] = (-385.0 - 75.0 * r) / 1152.0;
+  A[8][7] = (63.0 + 13.0 * r) / 128.0;
+  A[9][0] = 1.0 / 14.0;
+  A[9][4] = 1.0 / 9.0;
+  A[9][5] = (-733.0 - 147.0 * r) / 2205.0;
+  A[9][6] = (515.0 + 111.0 * r) / 504.0;
+  A[9][7] = (-51.0 - 11.0 * r) / 56.0;
+  A[9][8] = (132.0 + 28.0 * r) / 245.0;
+  A[10][4] = (-42.0 + 7.0 * r) / 18.0;
+  A[10][5] = (-18.0 + 28.0 * r) / 45.0;
+  A[10][6] = (-273.0 - 53.0 * r) / 72.0;
+  A[10][7] = (301.0 + 53.0 * r) / 72.0;
+  A[10][8] = (28.0 - 28.0 * r) / 45.0;
+  A[10][9] = (49.0 - 7.0 * r) / 18.0;
+  for (int s = 1; s < 11; ++s)
+    for (int j = 0; j < s; ++j) a[s * (s - 1) / 2 + j] = A[s][j];
+  for (int j = 0; j < 11; ++j) b[j] = 0.0;
+  b[0] = 1.0 / 20.0;
+  b[7] = 49.0 / 180.0;
+  b[8] = 16.0 / 45.0;
+  b[9] = 49.0 / 180.0;
+  b[10] = 1.0 / 20.0;
+  c[0] = 0.0;
+  c[1] = c[2] = c[5] = c[8] = 0.5;
+  c[3] = c[4] = c[9] = (7.0 + r) / 14.0;
+  c[6] = c[7] = (7.0 - r) / 14.0;
+  c[10] = 1.0;
+}
+
+void orc_rk8(const orc_problem* p, double* u, double dt, int nsteps) {
+  long d = orc_dim(p);
+  double a[55], b[11], c[11];
+  orc_rk8_tableau(a, b, c);
+  double* k = (double*)malloc(sizeof(double) * 11 * d);
+  double* w = (double*)malloc(sizeof(double) * d);
+  for (int n = 0; n < nsteps; ++n) {
+    orc_rhs(p, u, k);                                         /* k_0 = h(u) */
+    for (int s = 1; s < 11; ++s) {
+      const double* as = a + s * (s - 1) / 2;
+      for (long j = 0; j < d; ++j) {
+        double acc = as[0] * k[j];
+        for (int i = 1; i < s; ++i) acc = acc + as[i] * k[(long)i * d + j];
+        w[j] = u[j] + dt * acc;
+      }
+      orc_rhs(p, w, k + (long)s * d);                         /* k_s */
+    }
+    for (long j = 0; j < d; ++j) {
+      double acc = b[0] * k[j];
+      for (int i = 1; i < 11; ++i) acc = acc + b[i] * k[(long)i * d + j];
+      u[j] = u[j] + dt * acc;
+    }
+  }
+  free(k); free(w);
+}
+
 /* Forward Euler (RK1): u += dt h(u). */
 void orc_euler(const orc_problem* p, double* u, double dt, int nsteps) {
   long d = orc_dim(p);
@@ -204,7 +293,10 @@ static double slice_len(const orc_problem* p) { return (p->tN - p->t0) / p->N; }
 void orc_fine(const orc_problem* p, const double* in, double* out) {
   long d = orc_dim(p);
   if (out != in) memcpy(out, in, sizeof(double) * d);
-  orc_rk4(p, out, slice_len(p) / p->nF, p->nF);
+  if (p->fscheme == ORC_F_RK8)
+    orc_rk8(p, out, slice_len(p) / p->nF, p->nF);
+  else
+    orc_rk4(p, out, slice_len(p) / p->nF, p->nF);
 }
 
 void orc_coarse(const orc_problem* p, const double* in, double* out) {

@@ -12,8 +12,9 @@
  *   - the semi-discretised right-hand sides h(u) of Eq. 1 for the five PDE
  *     families of Sec. 5 and App. E (Burgers, diffusion-reaction, 2D/3D
  *     Brusselator, shallow water) plus two linear test operators;
- *   - the fine solver F (classic RK4) and the coarse solver G (forward
- *     Euler) over one time slice [Sec. 2, Tables 4-7];
+ *   - the fine solver F (classic RK4, or the eighth-order RK8 the paper
+ *     uses for Burgers and diffusion-reaction, Sec. 5.1-5.2) and the coarse
+ *     solver G (forward Euler) over one time slice [Sec. 2, Tables 4-7];
  *   - the RandNet of Eq. HA with seeded U(-1,1) weights (Alg. 3), the
  *     m-nearest-neighbour restriction of App. B (eq. fhat_mnn) and the
  *     ridge(less) readout of Eq. ridgeless in its dual (m x m) form;
@@ -50,6 +51,9 @@ enum { ORC_CORR_RANDNET = 0, ORC_CORR_PARAREAL = 1 };
  * Neumann boundary, finite-volume discretisation). */
 enum { ORC_BC_PERIODIC = 0, ORC_BC_NEUMANN = 1 };
 enum { ORC_SCALE_MINMAX = 0, ORC_SCALE_NONE = 1 };
+/* Fine integrator: classic RK4, or RK8 = the explicit eleven-stage
+ * eighth-order method of Cooper & Verner (SIAM J. Numer. Anal. 9, 1972). */
+enum { ORC_F_RK4 = 0, ORC_F_RK8 = 1 };
 enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2, ORC_ENONFINITE = 4,
        ORC_ENOTCONV = 5 };
 
@@ -60,7 +64,7 @@ typedef struct {
   double param[8];          /* PDE coefficients, see orc_rhs               */
   double t0, tN;            /* time interval of Eq. 1                      */
   int N;                    /* number of time slices                       */
-  int nF, nG;               /* RK4 steps of F, Euler steps of G per slice  */
+  int nF, nG;               /* steps of F and of G per slice               */
   int M, m;                 /* hidden neurons, nearest neighbours          */
   double lambda;            /* ridge penalty                               */
   uint64_t seed;            /* weight seed                                 */
@@ -70,6 +74,7 @@ typedef struct {
   int scale_mode;           /* ORC_SCALE_*                                 */
   int gscheme;              /* G integrator: 0 forward Euler (RK1), 1 RK4  */
   int bc;                   /* ORC_BC_* (shallow water: periodic only)     */
+  int fscheme;              /* ORC_F_*: F integrator                       */
 } orc_problem;
 
 typedef struct {
@@ -99,6 +104,13 @@ void orc_rhs(const orc_problem* p, const double* u, double* out);
 /* nsteps classic RK4 / forward-Euler steps of size dt, in place. */
 void orc_rk4(const orc_problem* p, double* u, double dt, int nsteps);
 void orc_euler(const orc_problem* p, double* u, double dt, int nsteps);
+/* The Cooper-Verner RK8 tableau: a[s*(s-1)/2 + j] = a_{s,j} (0 <= j < s,
+ * stages s = 1..10, 0-based), b[0..10], c[0..10]. */
+void orc_rk8_tableau(double* a, double* b, double* c);
+/* nsteps RK8 steps of size dt, in place.  Stage s is evaluated at
+ * u + dt (a_{s,0} k_0 + a_{s,1} k_1 + ... + a_{s,s-1} k_{s-1}) (sum left to
+ * right) and the step adds dt (b_0 k_0 + ... + b_10 k_10). */
+void orc_rk8(const orc_problem* p, double* u, double dt, int nsteps);
 /* F and G over one slice of length (tN - t0) / N. */
 void orc_fine(const orc_problem* p, const double* in, double* out);
 void orc_coarse(const orc_problem* p, const double* in, double* out);
