@@ -95,6 +95,15 @@ typedef enum { RNP_SCALE_MINMAX = 0, RNP_SCALE_NONE = 1 } rnp_scale;
 
 typedef enum { RNP_G_EULER = 0, RNP_G_RK4 = 1 } rnp_gscheme;
 
+typedef enum { RNP_F_RK4 = 0, RNP_F_RK8 = 1 } rnp_fscheme;
+/* F's integrator.  RK4: classic fourth order.  RK8: the eleven-stage
+ * explicit eighth-order method of Cooper & Verner (SIAM J. Numer. Anal. 9,
+ * 1972), the paper's RK8 fine solver (Sec. 5.1, 5.2) with a fixed step;
+ * requires precision RNP_FP64 (RNP_EINVAL otherwise).  In the fused
+ * execution a thread keeps the ten stage derivatives of at most two cells
+ * in registers, so a slice must fit 2 x 512 cells per CTA of a 16-CTA
+ * cluster (RNP_EINVAL otherwise; the plain execution has no such limit). */
+
 typedef enum { RNP_BC_PERIODIC = 0, RNP_BC_NEUMANN = 1 } rnp_bc;
 /* PERIODIC: every axis wraps.  NEUMANN: no-flux walls on a cell-centred
  * finite-volume grid (Sec. 5.2's no-flow Neumann boundary): the flux through
@@ -111,7 +120,7 @@ typedef struct {
   double param[8];        /* PDE coefficients (see rnp_pde)                 */
   double t0, tN;          /* time interval of Eq. 1                         */
   int N;                  /* time slices (Sec. 2)                           */
-  int nF, nG;             /* steps of F (RK4) and G per slice               */
+  int nF, nG;             /* steps of F (RK4 or RK8) and G per slice        */
   int M, m;               /* hidden neurons (Eq. HA), neighbours (App. B)   */
   double lambda;          /* ridge penalty of Eq. ridgeless (> 0)           */
   uint64_t seed;          /* seed of A and zeta (Alg. 3)                    */
@@ -131,6 +140,7 @@ typedef struct {
                              tiling on the context's buffers and keeps the
                              fastest (ignored when cluster/threads are set) */
   int bc;                 /* rnp_bc                                        */
+  int fscheme;            /* rnp_fscheme                                   */
 } rnp_problem;
 
 typedef struct {

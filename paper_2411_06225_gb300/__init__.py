@@ -50,7 +50,7 @@ class Problem(C.Structure):
         ("scale_mode", C.c_int), ("gscheme", C.c_int), ("precision", C.c_int),
         ("exec_", C.c_int), ("batch", C.c_int), ("cluster", C.c_int),
         ("threads", C.c_int), ("max_pairs", C.c_longlong), ("autotune", C.c_int),
-        ("bc", C.c_int),
+        ("bc", C.c_int), ("fscheme", C.c_int),
     ]
 
 
@@ -98,6 +98,7 @@ def problem(cfg: dict, precision: str = "fp64", exec: str = "fused", **kw) -> Pr
     p.max_pairs = c.get("max_pairs", 0)
     p.autotune = int(c.get("autotune", 0))
     p.bc = {"periodic": 0, "neumann": 1}[c.get("bc", "periodic")]
+    p.fscheme = {"rk4": 0, "rk8": 1}[c.get("fscheme", "rk4")]
     return p
 
 

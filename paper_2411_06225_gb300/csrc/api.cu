@@ -35,6 +35,7 @@ struct rnp_ctx {
   bool tunedF = false, tunedG = false;
   double dtF = 0, dtG = 0;
   int schemeG = SCHEME_EULER;
+  int schemeF = SCHEME_RK4;
 
   // device state
   double *U = nullptr, *Fv = nullptr, *Gc = nullptr, *Yv = nullptr, *gbuf = nullptr,
@@ -172,6 +173,9 @@ const char* validate(const rnp_problem* p) {
   if (p->scale_mode != RNP_SCALE_MINMAX && p->scale_mode != RNP_SCALE_NONE)
     return "unknown scale_mode";
   if (p->gscheme != RNP_G_EULER && p->gscheme != RNP_G_RK4) return "unknown gscheme";
+  if (p->fscheme != RNP_F_RK4 && p->fscheme != RNP_F_RK8) return "unknown fscheme";
+  if (p->fscheme == RNP_F_RK8 && p->precision != RNP_FP64)
+    return "the RK8 fine solver runs in FP64 only";
   if (p->precision != RNP_FP64 && p->precision != RNP_MIXED && p->precision != RNP_MIXED_BF16)
     return "unknown precision";
   if (p->exec != RNP_EXEC_FUSED && p->exec != RNP_EXEC_PLAIN) return "unknown exec";
@@ -216,7 +220,7 @@ void destroy_buffers(rnp_ctx* c) {
 rnp_status run_stencil(rnp_ctx* c, bool fine, const double* in, double* out, double* out2,
                        const Items& it, cudaStream_t stream = nullptr) {
   cudaStream_t sx = stream ? stream : c->st;
-  const int scheme = fine ? SCHEME_RK4 : c->schemeG;
+  const int scheme = fine ? c->schemeF : c->schemeG;
   const int steps = fine ? c->p.nF : c->p.nG;
   const double dt = fine ? c->dtF : c->dtG;
   cudaError_t e;
@@ -448,7 +452,8 @@ rnp_status autotune_stencils(rnp_ctx* c) {
     const bool fine = which == 0;
     const int nitems = fine ? B * N : B;
     StencilCfg cands[64];
-    const int n = list_stencil_cfgs(c->g, c->fp32, nitems, cands, 64);
+    const int n = list_stencil_cfgs(c->g, c->fp32, nitems, cands, 64,
+                                    fine && c->schemeF == SCHEME_RK8);
     if (n <= 1) continue;
     // long enough (about half a millisecond for a fine step) that launch and
     // cluster-scheduling noise do not decide the ranking
@@ -460,7 +465,7 @@ rnp_status autotune_stencils(rnp_ctx* c) {
       float tmin = 1e30f;
       for (int rep = 0; rep < 5; ++rep) {
         CK(cudaEventRecord(c->ev[4], c->st));
-        CK(launch_stencil_fused(c->g, c->coef, c->fp32, fine ? SCHEME_RK4 : c->schemeG, steps,
+        CK(launch_stencil_fused(c->g, c->coef, c->fp32, fine ? c->schemeF : c->schemeG, steps,
                                 fine ? c->dtF : c->dtG, c->U, c->Fv, nullptr, it, cands[k],
                                 c->st, c->flags + 3));
         CK(cudaEventRecord(c->ev[5], c->st));
@@ -521,6 +526,7 @@ rnp_status rnp_create(const rnp_problem* prob, void* cuda_stream, rnp_ctx** out)
   c->plain = prob->exec == RNP_EXEC_PLAIN;
   c->randnet = prob->corr == RNP_CORR_RANDNET;
   c->schemeG = prob->gscheme == RNP_G_RK4 ? SCHEME_RK4 : SCHEME_EULER;
+  c->schemeF = prob->fscheme == RNP_F_RK8 ? SCHEME_RK8 : SCHEME_RK4;
   const double dT = (prob->tN - prob->t0) / prob->N;
   c->dtF = dT / prob->nF;
   c->dtG = dT / prob->nG;
@@ -545,7 +551,7 @@ rnp_status rnp_create(const rnp_problem* prob, void* cuda_stream, rnp_ctx** out)
   };
   if (!c->plain) {
     if (!pick_stencil(c->g, c->fp32, B * N, false, prob->cluster, prob->threads, &c->cfgF, why,
-                      sizeof(why)))
+                      sizeof(why), c->schemeF == SCHEME_RK8))
       return bail(RNP_EINVAL, why);
     if (!pick_stencil(c->g, c->fp32, B, true, prob->cluster, prob->threads, &c->cfgG, why,
                       sizeof(why)))
@@ -591,7 +597,9 @@ rnp_status rnp_create(const rnp_problem* prob, void* cuda_stream, rnp_ctx** out)
   ok &= dalloc(&c->flags, (size_t)4) == cudaSuccess;
   ok &= dalloc(&c->dP, (size_t)B) == cudaSuccess;
   ok &= dalloc(&c->err, (size_t)B * (N + 1)) == cudaSuccess;
-  if (c->plain) ok &= dalloc(&c->plain_work, (size_t)4 * B * N * d) == cudaSuccess;
+  if (c->plain)
+    ok &= dalloc(&c->plain_work, (size_t)plain_work_doubles(c->schemeF, (long long)B * N * d)) ==
+          cudaSuccess;
   ok &= dalloc(&c->d_items, (size_t)4 * c->itemcap) == cudaSuccess;
   ok &= dalloc(&c->d_app, (size_t)3 * c->itemcap) == cudaSuccess;
   ok &= dalloc(&c->d_gate, (size_t)(N + 1) * B) == cudaSuccess;

@@ -23,7 +23,9 @@ enum KPde {
   KP_DIFFREACT = 5, KP_BRUSS2 = 6, KP_BRUSS3 = 7, KP_SWE = 8, KP_COUNT = 9
 };
 
-enum Scheme { SCHEME_EULER = 0, SCHEME_RK4 = 1 };
+// Time integrators: forward Euler (G), classic RK4 (F, or G), and the
+// eleven-stage eighth-order RK8 of Cooper & Verner (F, FP64 only).
+enum Scheme { SCHEME_EULER = 0, SCHEME_RK4 = 1, SCHEME_RK8 = 2 };
 
 // Geometry of one state vector.
 struct Geom {
@@ -81,16 +83,18 @@ Geom make_geom(const rnp_problem& p);
 Coef make_coef(const rnp_problem& p, const Geom& g);
 
 // Choose a fused-stencil configuration.  latency = true favours many SMs per
-// item (sequential sweep), false favours throughput (many items).
+// item (sequential sweep), false favours throughput (many items).  rk8: the
+// configuration runs the FP64 RK8 kernel (fp32 must be false).
 bool pick_stencil(const Geom& g, bool fp32, int nitems, bool latency,
                   int want_cluster, int want_threads, StencilCfg* out,
-                  char* why, int why_len);
+                  char* why, int why_len, bool rk8 = false);
 
 // Every launchable configuration (FP32 tiles when fp32, else the FP64
 // kernel), at most maxn, for the autotuner.
-int list_stencil_cfgs(const Geom& g, bool fp32, int nitems, StencilCfg* out, int maxn);
+int list_stencil_cfgs(const Geom& g, bool fp32, int nitems, StencilCfg* out, int maxn,
+                      bool rk8 = false);
 
-// Fused stencil: every item advances `steps` RK4/Euler steps of size dt
+// Fused stencil: every item advances `steps` Euler/RK4/RK8 steps of size dt
 // inside one launch, the slice resident in the cluster's shared memory.
 cudaError_t launch_stencil_fused(const Geom& g, const Coef& c, bool fp32,
                                  int scheme, int steps, double dt,
@@ -99,7 +103,8 @@ cudaError_t launch_stencil_fused(const Geom& g, const Coef& c, bool fp32,
                                  cudaStream_t st, int* err = nullptr);
 
 // Plain stencil: one launch per Runge-Kutta stage over global memory.
-// work must hold 4 * n_items * d doubles.
+// work must hold plain_work_doubles(scheme, n_items * d) doubles.
+long long plain_work_doubles(int scheme, long long items_d);
 cudaError_t launch_stencil_plain(const Geom& g, const Coef& c, int scheme,
                                  int steps, double dt, const double* in,
                                  double* out, double* out2, const Items& it,

@@ -1,4 +1,5 @@
-// stencil.cu -- fine (F, classic RK4) and coarse (G, forward Euler or RK4)
+// stencil.cu -- fine (F, classic RK4 or eighth-order RK8) and coarse (G,
+// forward Euler or RK4)
 // propagators of Sec. 2 over the periodic finite-difference right-hand sides
 // h(u) of Eq. 1 (Sec. 5.1 Burgers, Sec. 5.2 diffusion-reaction, App. E
 // Brusselator, Sec. 5.3 shallow water, plus heat and advection operators).
@@ -15,10 +16,14 @@
 //
 // Plain path: one launch per Runge-Kutta stage over global memory.
 //
+// RK8 is the eleven-stage explicit eighth-order method of Cooper & Verner
+// (SIAM J. Numer. Anal. 9, 1972), in FP64 only.
+//
 // FP64 variants evaluate every expression with explicitly rounded
 // operations (no contraction), in the same order as the plain serial
 // formulas, so F and G are bit-identical to a serial FP64 evaluation.  FP32
 // variants let the compiler contract multiply-adds.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 
@@ -102,6 +107,58 @@ Coef make_coef(const rnp_problem& p, const Geom& g) {
       c.k[0] = P[0]; c.k[1] = 0.5 * P[0]; c.k[2] = 1.0 / hx; c.k[3] = 1.0 / hy; break;
   }
   return c;
+}
+
+// The Cooper-Verner RK8 tableau from its published closed forms (rational
+// numbers and rational combinations of sqrt(21)): a_{s,j} at
+// rk[s*(s-1)/2 + j] for s = 1..10, j < s; b_0..b_10 at rk[55..65].
+static void rk8_tableau(double* rk) {
+  const double q = sqrt(21.0);
+  double a[11][11] = {};
+  a[1][0] = 1.0 / 2.0;
+  a[2][0] = 1.0 / 4.0;  a[2][1] = 1.0 / 4.0;
+  a[3][0] = 1.0 / 7.0;  a[3][1] = (-7.0 - 3.0 * q) / 98.0;  a[3][2] = (21.0 + 5.0 * q) / 49.0;
+  a[4][0] = (11.0 + q) / 84.0;  a[4][2] = (18.0 + 4.0 * q) / 63.0;
+  a[4][3] = (21.0 - q) / 252.0;
+  a[5][0] = (5.0 + q) / 48.0;  a[5][2] = (9.0 + q) / 36.0;
+  a[5][3] = (-231.0 + 14.0 * q) / 360.0;  a[5][4] = (63.0 - 7.0 * q) / 80.0;
+  a[6][0] = (10.0 - q) / 42.0;  a[6][2] = (-432.0 + 92.0 * q) / 315.0;
+  a[6][3] = (633.0 - 145.0 * q) / 90.0;  a[6][4] = (-504.0 + 115.0 * q) / 70.0;
+  a[6][5] = (63.0 - 13.0 * q) / 35.0;
+  a[7][0] = 1.0 / 14.0;  a[7][4] = (14.0 - 3.0 * q) / 126.0;
+  a[7][5] = (13.0 - 3.0 * q) / 63.0;  a[7][6] = 1.0 / 9.0;
+  a[8][0] = 1.0 / 32.0;  a[8][4] = (91.0 - 21.0 * q) / 576.0;  a[8][5] = 11.0 / 72.0;
+  a[8][6] = (-385.0 - 75.0 * q) / 1152.0;  a[8][7] = (63.0 + 13.0 * q) / 128.0;
+  a[9][0] = 1.0 / 14.0;  a[9][4] = 1.0 / 9.0;  a[9][5] = (-733.0 - 147.0 * q) / 2205.0;
+  a[9][6] = (515.0 + 111.0 * q) / 504.0;  a[9][7] = (-51.0 - 11.0 * q) / 56.0;
+  a[9][8] = (132.0 + 28.0 * q) / 245.0;
+  a[10][4] = (-42.0 + 7.0 * q) / 18.0;  a[10][5] = (-18.0 + 28.0 * q) / 45.0;
+  a[10][6] = (-273.0 - 53.0 * q) / 72.0;  a[10][7] = (301.0 + 53.0 * q) / 72.0;
+  a[10][8] = (28.0 - 28.0 * q) / 45.0;  a[10][9] = (49.0 - 7.0 * q) / 18.0;
+  for (int s = 1; s <= 10; ++s)
+    for (int j = 0; j < s; ++j) rk[s * (s - 1) / 2 + j] = a[s][j];
+  double* b = rk + 55;
+  for (int j = 0; j < 11; ++j) b[j] = 0.0;
+  b[0] = 1.0 / 20.0;
+  b[7] = 49.0 / 180.0;
+  b[8] = 16.0 / 45.0;
+  b[9] = 49.0 / 180.0;
+  b[10] = 1.0 / 20.0;
+}
+
+static FusedFn fused_rk8_fn(int kp, int R) {
+  switch (kp) {
+    case KP_BURGERS: return fused_rk8_fn_burgers(R);
+    case KP_ADVECT: return fused_rk8_fn_advect(R);
+    case KP_HEAT1: return fused_rk8_fn_heat1(R);
+    case KP_HEAT2: return fused_rk8_fn_heat2(R);
+    case KP_HEAT3: return fused_rk8_fn_heat3(R);
+    case KP_DIFFREACT: return fused_rk8_fn_diffreact(R);
+    case KP_BRUSS2: return fused_rk8_fn_bruss2(R);
+    case KP_BRUSS3: return fused_rk8_fn_bruss3(R);
+    case KP_SWE: return fused_rk8_fn_swe(R);
+  }
+  return nullptr;
 }
 
 // The FP64 fused kernel (every operation explicitly rounded).
@@ -206,7 +263,7 @@ static bool launchable(FusedFn fn, int CS, int threads, size_t smem, int nitems)
 static thread_local int g_tile_relax = 0;  // 1: allow register tiles that spill a little
 
 static bool try_cfg(const Geom& g, bool fp32, int CS, int threads, int nitems,
-                    StencilCfg* out, int want_px = 0, int want_rs = 0) {
+                    StencilCfg* out, int want_px = 0, int want_rs = 0, bool rk8 = false) {
   if (g.outer % CS) return false;
   if (g.dims == 1 && CS != 1) return false;
   const long long nloc = g.outer / CS;
@@ -251,6 +308,27 @@ static bool try_cfg(const Geom& g, bool fp32, int CS, int threads, int nitems,
   }
   if (fp32) return false;
   if (smem_bytes(g, false, CS) > (size_t)kMaxSmem) return false;
+  if (rk8) {
+    // RK8 kernel: the ten stage derivatives of each cell live in registers,
+    // so a thread owns at most two cells
+    if (threads <= 0) {
+      long long t = (ncell + 1) / 2;
+      t = ((t + 31) / 32) * 32;
+      if (t < 32) t = 32;
+      threads = (int)t;
+    }
+    if (threads > 512) return false;
+    const long long per = (ncell + threads - 1) / threads;
+    const int R = per <= 1 ? 1 : (per <= 2 ? 2 : -1);
+    if (R < 0) return false;
+    FusedFn fn = fused_rk8_fn(g.kp, R);
+    if (!fn || !launchable(fn, CS, threads, smem_bytes(g, false, CS), nitems)) return false;
+    out->cluster = CS;
+    out->threads = threads;
+    out->R = R;
+    out->px = out->rs = 0;
+    return true;
+  }
   if (threads <= 0) {
     // enough threads that every thread owns <= 4 points
     long long t = (ncell + 3) / 4;
@@ -271,31 +349,34 @@ static bool try_cfg(const Geom& g, bool fp32, int CS, int threads, int nitems,
 }
 
 static bool pick_one(const Geom& g, bool fp32, int nitems, bool latency, int want_cluster,
-                     int want_threads, StencilCfg* out, char* why, int why_len);
+                     int want_threads, StencilCfg* out, char* why, int why_len, bool rk8);
 
 bool pick_stencil(const Geom& g, bool fp32, int nitems, bool latency, int want_cluster,
-                  int want_threads, StencilCfg* out, char* why, int why_len) {
+                  int want_threads, StencilCfg* out, char* why, int why_len, bool rk8) {
+  if (rk8) return pick_one(g, false, nitems, latency, want_cluster, want_threads, out, why,
+                           why_len, true);
   // a mixed-precision context prefers an FP32 tile at any cluster size and
   // falls back to the FP64 kernel only when no FP32 tile fits
   if (fp32) {
     g_tile_relax = 0;
-    if (pick_one(g, true, nitems, latency, want_cluster, want_threads, out, why, why_len))
+    if (pick_one(g, true, nitems, latency, want_cluster, want_threads, out, why, why_len, false))
       return true;
     for (int level = 1; level <= 2; ++level) {
       g_tile_relax = level;
-      const bool ok =
-          pick_one(g, true, nitems, latency, want_cluster, want_threads, out, why, why_len);
+      const bool ok = pick_one(g, true, nitems, latency, want_cluster, want_threads, out, why,
+                               why_len, false);
       g_tile_relax = 0;
       if (ok) return true;
     }
   }
-  return pick_one(g, false, nitems, latency, want_cluster, want_threads, out, why, why_len);
+  return pick_one(g, false, nitems, latency, want_cluster, want_threads, out, why, why_len,
+                  false);
 }
 
 static bool pick_one(const Geom& g, bool fp32, int nitems, bool latency, int want_cluster,
-                     int want_threads, StencilCfg* out, char* why, int why_len) {
+                     int want_threads, StencilCfg* out, char* why, int why_len, bool rk8) {
   if (want_cluster > 0) {
-    if (try_cfg(g, fp32, want_cluster, want_threads, nitems, out)) return true;
+    if (try_cfg(g, fp32, want_cluster, want_threads, nitems, out, 0, 0, rk8)) return true;
     snprintf(why, why_len, "stencil configuration cluster=%d threads=%d is not launchable",
              want_cluster, want_threads);
     return false;
@@ -309,14 +390,20 @@ static bool pick_one(const Geom& g, bool fp32, int nitems, bool latency, int wan
   for (int ci = 0; ci < nc; ++ci) {
     const int CS = cands[ci];
     StencilCfg c;
-    if (!try_cfg(g, fp32, CS, want_threads, nitems, &c)) continue;
+    if (!try_cfg(g, fp32, CS, want_threads, nitems, &c, 0, 0, rk8)) continue;
     if (best < 0) { *out = c; best = CS; if (!latency) break; }
     else if (latency && CS <= 8) { *out = c; best = CS; }
   }
   if (best < 0) {
-    snprintf(why, why_len,
-             "state of %lld unknowns does not fit the shared memory of a 16-CTA cluster",
-             (long long)g.d);
+    if (rk8)
+      snprintf(why, why_len,
+               "the fused RK8 kernel holds at most 2 x 512 cells per CTA of a 16-CTA cluster "
+               "(state of %lld unknowns); use the plain execution",
+               (long long)g.d);
+    else
+      snprintf(why, why_len,
+               "state of %lld unknowns does not fit the shared memory of a 16-CTA cluster",
+               (long long)g.d);
     return false;
   }
   // throughput: grow the cluster while the grid is below one CTA per SM
@@ -329,13 +416,14 @@ static bool pick_one(const Geom& g, bool fp32, int nitems, bool latency, int wan
       const int CS = cands[ci];
       if (CS <= out->cluster || CS > 8 || (long long)nitems * CS > sms) continue;
       StencilCfg c;
-      if (try_cfg(g, fp32, CS, want_threads, nitems, &c)) *out = c;
+      if (try_cfg(g, fp32, CS, want_threads, nitems, &c, 0, 0, rk8)) *out = c;
     }
   }
   return true;
 }
 
-int list_stencil_cfgs(const Geom& g, bool fp32, int nitems, StencilCfg* out, int maxn) {
+int list_stencil_cfgs(const Geom& g, bool fp32, int nitems, StencilCfg* out, int maxn,
+                      bool rk8) {
   int n = 0;
   for (int CS = 1; CS <= 16 && n < maxn; ++CS) {
     if (g.outer % CS) continue;
@@ -354,7 +442,7 @@ int list_stencil_cfgs(const Geom& g, bool fp32, int nitems, StencilCfg* out, int
         }
     } else {
       StencilCfg c;
-      if (try_cfg(g, false, CS, 0, nitems, &c)) out[n++] = c;
+      if (try_cfg(g, false, CS, 0, nitems, &c, 0, 0, rk8)) out[n++] = c;
     }
   }
   return n;
@@ -367,9 +455,11 @@ cudaError_t launch_stencil_fused(const Geom& g, const Coef& c, bool fp32, int sc
   if (it.n <= 0 || steps <= 0) return cudaSuccess;
   // a mixed-precision context uses the FP64 kernel where no FP32 tile fits
   const bool use_mixed = fp32 && cfg.px > 0;
+  if (scheme == SCHEME_RK8 && use_mixed) return cudaErrorInvalidValue;  // FP64 only
   FusedFn fn = use_mixed ? mixed_fn(g.kp, cfg.px, cfg.rs, x_shuffles(g, cfg.px), g.bc != 0,
                                     scheme == SCHEME_RK4)
-                         : fused_fn(g.kp, cfg.R);
+               : scheme == SCHEME_RK8 ? fused_rk8_fn(g.kp, cfg.R)
+                                      : fused_fn(g.kp, cfg.R);
   if (!fn) return cudaErrorInvalidValue;
   FusedParams P;
   P.in = in; P.out = out; P.out2 = out2;
@@ -387,6 +477,8 @@ cudaError_t launch_stencil_fused(const Geom& g, const Coef& c, bool fp32, int sc
   P.mcl = P.nloc * (int)g.plane;
   P.moff = (int)((((size_t)2 * g.ncomp * P.mcell + (size_t)g.ncomp * P.mcl) * 4 + 15) &
                  ~(size_t)15);
+  if (scheme == SCHEME_RK8) rk8_tableau(P.rk);
+  else memset(P.rk, 0, sizeof(P.rk));
   cudaLaunchConfig_t lc = {};
   cudaLaunchAttribute at[1];
   lc.gridDim = dim3(cfg.cluster * it.n);
@@ -425,6 +517,10 @@ static int grid_for(long long tot, int threads) {
   return (int)b;
 }
 
+long long plain_work_doubles(int scheme, long long items_d) {
+  return (scheme == SCHEME_RK8 ? 14 : 4) * items_d;
+}
+
 cudaError_t launch_stencil_plain(const Geom& g, const Coef& c, int scheme, int steps,
                                  double dt, const double* in, double* out, double* out2,
                                  const Items& it, double* work, cudaStream_t st) {
@@ -442,7 +538,10 @@ cudaError_t launch_stencil_plain(const Geom& g, const Coef& c, int scheme, int s
   P.nx = g.nx; P.ny = g.ny; P.nz = g.nz; P.n = g.n; P.d = g.d;
   P.scheme = scheme; P.dt = dt; P.h2 = dt / 2.0; P.h6 = dt / 6.0; P.coef = c;
   P.bc = g.bc;
-  const int S = scheme == SCHEME_RK4 ? 4 : 1;
+  P.Kst = work + 4 * tot;   // RK8 only: ten more state-sized arrays
+  if (scheme == SCHEME_RK8) rk8_tableau(P.rk);
+  else memset(P.rk, 0, sizeof(P.rk));
+  const int S = scheme == SCHEME_RK8 ? 11 : (scheme == SCHEME_RK4 ? 4 : 1);
   const long long cells = (long long)it.n * g.n;
   int cur = 0;
   for (int step = 0; step < steps; ++step)

@@ -155,11 +155,62 @@ struct FusedParams {
   // parameter space instead of being kept in registers
   int nloc, mcell, mcl;
   int moff;          // byte offset of the mbarriers in the dynamic shared memory
+  // eighth-order fine solver (FP64 kernel): a_{s,j} at rk[s*(s-1)/2 + j] for
+  // stages s = 1..10, j < s, then b_0..b_10 at rk[55..65]
+  double rk[66];
 };
+
+// Neighbours of cell c of this CTA's block (periodic wrap, or the cell
+// itself across a no-flux wall; outer neighbours across a CTA boundary from
+// the adjacent CTA's block BP / BN) and h(u) there.
+template <int KP, typename T, bool EX>
+__device__ __forceinline__ void fused_cell_rhs(const FusedParams& P, const T* B, const T* BP,
+                                               const T* BN, int c, int ncell, int nloc,
+                                               int rank, int CS, const T* kk, T* k) {
+  constexpr int NC = KT<KP>::NC, DIMS = KT<KP>::DIMS;
+  const int plane = P.plane, nx = P.nx, ny = P.ny;
+  const int o = c / plane;
+  const int ii = c - o * plane;
+  int x, y;
+  if (DIMS == 3) { y = ii / nx; x = ii - y * nx; } else { x = ii; y = 0; }
+  // neighbours: periodic wrap, or the cell itself across a no-flux wall
+  const bool wall = P.bc != 0;
+  const int xe = (x + 1 == nx) ? (wall ? x : 0) : x + 1;
+  const int xw = (x == 0) ? (wall ? 0 : nx - 1) : x - 1;
+  const int rowb = o * plane + (DIMS == 3 ? y * nx : 0);
+  T Cv[NC], Ev[NC], Wv[NC], Nv[NC], Sv[NC], Uv[NC], Dv[NC];
+#pragma unroll
+  for (int q = 0; q < NC; ++q) {
+    const T* Bq = B + q * ncell;
+    Cv[q] = Bq[c];
+    Ev[q] = Bq[rowb + xe];
+    Wv[q] = Bq[rowb + xw];
+    Nv[q] = Sv[q] = Uv[q] = Dv[q] = T(0);
+    if (DIMS == 3) {
+      const int yn = (y + 1 == ny) ? (wall ? y : 0) : y + 1;
+      const int ys = (y == 0) ? (wall ? 0 : ny - 1) : y - 1;
+      Nv[q] = Bq[o * plane + yn * nx + x];
+      Sv[q] = Bq[o * plane + ys * nx + x];
+    }
+    if (DIMS >= 2) {
+      // outer neighbours: local, the neighbouring CTA's first/last
+      // plane, or (at a wall) the cell itself
+      T vp, vm;
+      if (o + 1 < nloc) vp = Bq[c + plane];
+      else if (wall && rank == CS - 1) vp = Cv[q];
+      else vp = BN[q * ncell + ii];
+      if (o > 0) vm = Bq[c - plane];
+      else if (wall && rank == 0) vm = Cv[q];
+      else vm = BP[q * ncell + (nloc - 1) * plane + ii];
+      if (DIMS == 2) { Nv[q] = vp; Sv[q] = vm; } else { Uv[q] = vp; Dv[q] = vm; }
+    }
+  }
+  rhs_point<KP, T, EX>(Cv, Ev, Wv, Nv, Sv, Uv, Dv, kk, k);
+}
 
 template <int KP, typename T, bool EX, int R>
 __global__ void __launch_bounds__(512, 1) k_stencil_fused(const FusedParams P) {
-  constexpr int NC = KT<KP>::NC, DIMS = KT<KP>::DIMS;
+  constexpr int NC = KT<KP>::NC;
   using A = Ar<T, EX>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int CS = P.cluster;
@@ -167,9 +218,8 @@ __global__ void __launch_bounds__(512, 1) k_stencil_fused(const FusedParams P) {
   const int item = blockIdx.x / CS;
   if (item >= P.it.n) return;                // uniform over the cluster
   if (P.it.gate && !P.it.gate[item]) return; // uniform over the cluster
-  const int plane = P.plane, nx = P.nx, ny = P.ny;
   const int nloc = P.outer / CS;
-  const int ncell = nloc * plane;
+  const int ncell = nloc * P.plane;
   T* const buf0 = reinterpret_cast<T*>(smem_raw);
   T* const buf1 = buf0 + NC * ncell;
   const T *rp0 = buf0, *rp1 = buf1, *rn0 = buf0, *rn1 = buf1;
@@ -218,44 +268,8 @@ __global__ void __launch_bounds__(512, 1) k_stencil_fused(const FusedParams P) {
       for (int j = 0; j < R; ++j) {
         const int c = tid + j * TT;
         if (c >= ncell) continue;
-        const int o = c / plane;
-        const int ii = c - o * plane;
-        int x, y;
-        if (DIMS == 3) { y = ii / nx; x = ii - y * nx; } else { x = ii; y = 0; }
-        // neighbours: periodic wrap, or the cell itself across a no-flux wall
-        const bool wall = P.bc != 0;
-        const int xe = (x + 1 == nx) ? (wall ? x : 0) : x + 1;
-        const int xw = (x == 0) ? (wall ? 0 : nx - 1) : x - 1;
-        const int rowb = o * plane + (DIMS == 3 ? y * nx : 0);
-        T Cv[NC], Ev[NC], Wv[NC], Nv[NC], Sv[NC], Uv[NC], Dv[NC];
-#pragma unroll
-        for (int q = 0; q < NC; ++q) {
-          const T* Bq = B + q * ncell;
-          Cv[q] = Bq[c];
-          Ev[q] = Bq[rowb + xe];
-          Wv[q] = Bq[rowb + xw];
-          Nv[q] = Sv[q] = Uv[q] = Dv[q] = T(0);
-          if (DIMS == 3) {
-            const int yn = (y + 1 == ny) ? (wall ? y : 0) : y + 1;
-            const int ys = (y == 0) ? (wall ? 0 : ny - 1) : y - 1;
-            Nv[q] = Bq[o * plane + yn * nx + x];
-            Sv[q] = Bq[o * plane + ys * nx + x];
-          }
-          if (DIMS >= 2) {
-            // outer neighbours: local, the neighbouring CTA's first/last
-            // plane, or (at a wall) the cell itself
-            T vp, vm;
-            if (o + 1 < nloc) vp = Bq[c + plane];
-            else if (wall && rank == CS - 1) vp = Cv[q];
-            else vp = BN[q * ncell + ii];
-            if (o > 0) vm = Bq[c - plane];
-            else if (wall && rank == 0) vm = Cv[q];
-            else vm = BP[q * ncell + (nloc - 1) * plane + ii];
-            if (DIMS == 2) { Nv[q] = vp; Sv[q] = vm; } else { Uv[q] = vp; Dv[q] = vm; }
-          }
-        }
         T k[NC];
-        rhs_point<KP, T, EX>(Cv, Ev, Wv, Nv, Sv, Uv, Dv, kk, k);
+        fused_cell_rhs<KP, T, EX>(P, B, BP, BN, c, ncell, nloc, rank, CS, kk, k);
 #pragma unroll
         for (int q = 0; q < NC; ++q) {
           T w;
@@ -298,6 +312,118 @@ __global__ void __launch_bounds__(512, 1) k_stencil_fused(const FusedParams P) {
   }
 }
 
+// FP64 eighth-order fine solver (the eleven-stage explicit method of Cooper
+// & Verner, SIAM J. Numer. Anal. 9, 1972; the paper's F is RK8, Sec. 5.1-5.2).
+// Same residency and neighbour exchange as k_stencil_fused; the ten stage
+// derivatives k_0..k_9 of a step stay in registers (R <= 2 cells per
+// thread).  Stage s is evaluated at u + dt (a_{s,0} k_0 + ... + a_{s,s-1}
+// k_{s-1}), summed left to right, and the step adds dt (b_0 k_0 + ... +
+// b_10 k_10); every operation is explicitly rounded, so the result is
+// bit-identical to a plain serial evaluation of the same sums.
+template <int KP, int R>
+__global__ void __launch_bounds__(512, 1) k_stencil_fused_rk8(const FusedParams P) {
+  using T = double;
+  using A = Ar<double, true>;
+  constexpr int NC = KT<KP>::NC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int CS = P.cluster;
+  const int rank = CS > 1 ? (int)cg::this_cluster().block_rank() : 0;
+  const int item = blockIdx.x / CS;
+  if (item >= P.it.n) return;                // uniform over the cluster
+  if (P.it.gate && !P.it.gate[item]) return; // uniform over the cluster
+  const int nloc = P.outer / CS;
+  const int ncell = nloc * P.plane;
+  T* const buf0 = reinterpret_cast<T*>(smem_raw);
+  T* const buf1 = buf0 + NC * ncell;
+  const T *rp0 = buf0, *rp1 = buf1, *rn0 = buf0, *rn1 = buf1;
+  if (CS > 1) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rp = (rank + CS - 1) % CS, rn = (rank + 1) % CS;
+    rp0 = cl.map_shared_rank(buf0, rp);
+    rp1 = cl.map_shared_rank(buf1, rp);
+    rn0 = cl.map_shared_rank(buf0, rn);
+    rn1 = cl.map_shared_rank(buf1, rn);
+  }
+  T kk[12];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) kk[i] = P.coef.k[i];
+  const T dt = P.dt;
+  const long long base = (long long)rank * ncell;
+  const double* in = P.in + item_off(P.it.src_off, P.it.src_base, P.it.src_stride, item) + base;
+  const int tid = threadIdx.x, TT = blockDim.x;
+
+  T u[R][NC], ks[10][R][NC];
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int c = tid + j * TT;
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      T v = T(0);
+      if (c < ncell) {
+        v = in[q * P.n + c];
+        buf0[q * ncell + c] = v;
+      }
+      u[j][q] = v;
+    }
+  }
+  if (CS > 1) cg::this_cluster().sync(); else __syncthreads();
+
+  int cur = 0;
+  for (int step = 0; step < P.steps; ++step) {
+#pragma unroll
+    for (int s = 0; s < 11; ++s) {
+      const T* B = cur ? buf1 : buf0;
+      T* Bn = cur ? buf0 : buf1;
+      const T* BP = cur ? rp1 : rp0;
+      const T* BN = cur ? rn1 : rn0;
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const int c = tid + j * TT;
+        if (c >= ncell) continue;
+        T k[NC];
+        fused_cell_rhs<KP, T, true>(P, B, BP, BN, c, ncell, nloc, rank, CS, kk, k);
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+          T w;
+          if (s < 10) {
+            // input of stage s + 1
+            const double* an = P.rk + (s + 1) * s / 2;
+            ks[s][j][q] = k[q];
+            T acc = A::mul(an[0], ks[0][j][q]);
+#pragma unroll
+            for (int i = 1; i <= s; ++i) acc = A::add(acc, A::mul(an[i], ks[i][j][q]));
+            w = A::add(u[j][q], A::mul(dt, acc));
+          } else {
+            const double* bw = P.rk + 55;
+            T acc = A::mul(bw[0], ks[0][j][q]);
+#pragma unroll
+            for (int i = 1; i < 10; ++i) acc = A::add(acc, A::mul(bw[i], ks[i][j][q]));
+            acc = A::add(acc, A::mul(bw[10], k[q]));
+            u[j][q] = A::add(u[j][q], A::mul(dt, acc));
+            w = u[j][q];
+          }
+          Bn[q * ncell + c] = w;
+        }
+      }
+      cur ^= 1;
+      if (CS > 1) cg::this_cluster().sync(); else __syncthreads();
+    }
+  }
+  double* out = P.out + item_off(P.it.dst_off, P.it.dst_base, P.it.dst_stride, item) + base;
+  double* out2 = P.out2 ? P.out2 + item_off(P.it.dst2_off, P.it.dst2_base, P.it.dst2_stride, item) + base
+                        : nullptr;
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int c = tid + j * TT;
+    if (c >= ncell) continue;
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      out[q * P.n + c] = u[j][q];
+      if (out2) out2[q * P.n + c] = u[j][q];
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Plain per-stage kernels
 // ---------------------------------------------------------------------------
@@ -314,6 +440,8 @@ struct PlainParams {
   double dt, h2, h6;
   Coef coef;
   int bc;             // 0 periodic, 1 no-flux walls
+  double* Kst;        // RK8: stage derivatives k_0..k_9, [10][nitems * d]
+  double rk[66];      // RK8 tableau, laid out as in FusedParams::rk
 };
 
 template <int KP>
@@ -357,7 +485,18 @@ __global__ void k_stage_plain(const PlainParams P) {
       const long long e = (long long)item * P.d + q * P.n + cell;
       double w;
       const double u = P.U[e];
-      if (P.scheme == SCHEME_EULER) {
+      if (P.scheme == SCHEME_RK8) {
+        // stage s: keep k_s, then form the input of stage s + 1 (or the step)
+        const long long tot = (long long)P.nitems * P.d;
+        const int s = P.stage;
+        const double* cf = s < 10 ? P.rk + (s + 1) * s / 2 : P.rk + 55;
+        double acc = A::mul(cf[0], s == 0 ? k[q] : P.Kst[e]);
+        for (int i = 1; i <= s; ++i)
+          acc = A::add(acc, A::mul(cf[i], i == s ? k[q] : P.Kst[i * tot + e]));
+        if (s < 10) P.Kst[s * tot + e] = k[q];
+        w = A::add(u, A::mul(P.dt, acc));
+        if (s == 10) P.U[e] = w;
+      } else if (P.scheme == SCHEME_EULER) {
         w = A::add(u, A::mul(P.dt, k[q]));
         P.U[e] = w;
       } else if (P.stage == 0) {
@@ -885,6 +1024,15 @@ inline FusedFn fused_for_R(int R) {
   }
 }
 
+template <int KP>
+inline FusedFn fused_rk8_for_R(int R) {
+  switch (R) {
+    case 1: return k_stencil_fused_rk8<KP, 1>;
+    case 2: return k_stencil_fused_rk8<KP, 2>;
+    default: return nullptr;
+  }
+}
+
 // Register tiles of more than kMaxTileValues state values per thread spill
 // beyond use and are not instantiated (the host picker never asks for them).
 static constexpr int kMaxTileValues = 40;
@@ -930,6 +1078,7 @@ inline FusedFn mixed_for(int PX, int RS, bool XS, bool WALL, bool RK) {
 // Per-PDE entry points, defined in stencil_<pde>.cu.
 #define RNP_STENCIL_DECL(NAME)                 \
   FusedFn fused_fn_##NAME(int R);              \
+  FusedFn fused_rk8_fn_##NAME(int R);          \
   FusedFn mixed_fn_##NAME(int PX, int RS, bool XS, bool WALL, bool RK); \
   PlainFn plain_fn_##NAME();
 RNP_STENCIL_DECL(burgers)
@@ -945,6 +1094,7 @@ RNP_STENCIL_DECL(swe)
 
 #define RNP_STENCIL_DEFINE(KPV, NAME)                                                \
   FusedFn fused_fn_##NAME(int R) { return fused_for_R<KPV, double, true>(R); }       \
+  FusedFn fused_rk8_fn_##NAME(int R) { return fused_rk8_for_R<KPV>(R); }             \
   FusedFn mixed_fn_##NAME(int PX, int RS, bool XS, bool WALL, bool RK) {             \
     return mixed_for<KPV>(PX, RS, XS, WALL, RK);                                     \
   }                                                                                  \

@@ -7,8 +7,10 @@ Two systems, as in the paper:
   * ``burgers``   1D Burgers as in the paper's Burgers experiment: d = 128,
                   N = 128 slices on [0, 5.9], u0 = 0.5 (cos(9 pi x / 2) + 1),
                   nu = 0.01, G = Euler x 4 per slice; F = RK4 x 100 per slice
-                  (the paper uses RK8; the fine step only needs to be far
-                  more accurate than tol);
+                  by default (the fine step only needs to be far more
+                  accurate than tol), or with ``--fine rk8`` the paper's
+                  RK8 with its 4e4 fine steps spread over the 128 slices
+                  (313 per slice);
   * ``diffreact`` diffusion-reaction on a 19 x 19 grid (d = 722, the paper's
                   robustness size), N = 32 on [0, 5], F = RK4 x 200,
                   G = Euler x 4.
@@ -33,12 +35,16 @@ import time
 SYSTEMS = ("burgers", "diffreact")
 
 
-def system_config(name: str) -> dict:
+def system_config(name: str, fine: str = "rk4") -> dict:
     import workloads as W
+    if fine not in ("rk4", "rk8"):
+        raise ValueError(f"unknown fine solver {fine!r}")
     if name == "burgers":
-        return W.config("burgers1d", N=128, tN=5.9, nF=100, nG=4, ic="cos9", max_iters=128)
+        nF = 100 if fine == "rk4" else 313
+        return W.config("burgers1d", N=128, tN=5.9, nF=nF, nG=4, ic="cos9", max_iters=128,
+                        fscheme=fine)
     if name == "diffreact":
-        return W.config("diffreact2d", nx=19, ny=19, N=32, nF=200, nG=4, tN=5.0)
+        return W.config("diffreact2d", nx=19, ny=19, N=32, nF=200, nG=4, tN=5.0, fscheme=fine)
     raise ValueError(f"unknown system {name!r} (one of {SYSTEMS})")
 
 
@@ -85,7 +91,8 @@ def histograms(results) -> dict:
     }
 
 
-def run(system: str, points, precision: str = "fp64", workers: int = 8) -> list[tuple]:
+def run(system: str, points, precision: str = "fp64", workers: int = 8,
+        fine: str = "rk4") -> list[tuple]:
     """Solve every (m, M, seed) point on the GPU; returns (m, M, seed, K,
     outcome) per point, in the order of ``points`` (see ``histograms``)."""
     import numpy as np
@@ -94,7 +101,7 @@ def run(system: str, points, precision: str = "fp64", workers: int = 8) -> list[
     import workloads as W
 
     from . import RNP_ENONFINITE, RnpError, Solver, problem
-    cfg = system_config(system)
+    cfg = system_config(system, fine)
     u0_h = np.ascontiguousarray(W.initial_condition(cfg), dtype=np.float64)
     out = [None] * len(points)
     nxt = [0]
@@ -155,14 +162,17 @@ def main():
     ap.add_argument("--seeds", type=int, default=20, help="weight draws")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--workers", type=int, default=8)
+    ap.add_argument("--fine", default="rk4", choices=["rk4", "rk8"],
+                    help="fine solver (rk8: FP64 only)")
     args = ap.parse_args()
-    cfg = system_config(args.system)
+    cfg = system_config(args.system, args.fine)
     pts = grid(_range(args.m), _range(args.M), weight_seeds(args.seeds))
     t0 = time.perf_counter()
-    res = run(args.system, pts, args.precision, args.workers)
+    res = run(args.system, pts, args.precision, args.workers, args.fine)
     wall = time.perf_counter() - t0
     import workloads as W
-    print(json.dumps(dict(system=args.system, d=W.dim(cfg), N=cfg["N"], precision=args.precision,
+    print(json.dumps(dict(system=args.system, d=W.dim(cfg), N=cfg["N"], fine=args.fine,
+                          nF=cfg["nF"], precision=args.precision,
                           seeds=args.seeds, wall_s=wall, solves_per_s=len(pts) / wall,
                           **histograms(res))))
 

@@ -31,7 +31,7 @@ from . import (RNP_MEMBER_ACTIVE, RNP_MEMBER_CONVERGED, RNP_MEMBER_FREE, RNP_OK,
                RnpError, Solver, dim, lib, problem)
 
 CLASS_KEYS = ("pde", "nx", "ny", "nz", "lx", "ly", "lz", "t0", "tN", "N", "nF", "nG",
-              "M", "m", "lam", "tol", "max_iters", "corr", "gscheme")
+              "M", "m", "lam", "tol", "max_iters", "corr", "gscheme", "fscheme", "bc")
 
 
 def class_key(cfg: dict) -> tuple:
