@@ -54,7 +54,7 @@ class Problem(C.Structure):
         ("m", C.c_int), ("lam", C.c_double), ("seed", C.c_uint64),
         ("tol", C.c_double), ("max_iters", C.c_int), ("corr", C.c_int),
         ("scale_mode", C.c_int), ("gscheme", C.c_int), ("bc", C.c_int),
-        ("fscheme", C.c_int),
+        ("fscheme", C.c_int), ("bathy", C.POINTER(C.c_double)),
     ]
 
 
@@ -140,6 +140,12 @@ def problem(cfg: dict, **kw) -> Problem:
     p.gscheme = {"euler": 0, "rk4": 1}[c.get("gscheme", "euler")]
     p.bc = {"periodic": 0, "neumann": 1}[c.get("bc", "periodic")]
     p.fscheme = {"rk4": 0, "rk8": 1}[c.get("fscheme", "rk4")]
+    b = c.get("bathymetry")
+    if b is not None:
+        b = np.ascontiguousarray(b, np.float64).reshape(-1)
+        assert b.size == c["nx"] * c["ny"] * c["nz"]
+        p._bathy = b                      # keeps the array alive with p
+        p.bathy = b.ctypes.data_as(_DP)
     return p
 
 

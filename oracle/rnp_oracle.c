@@ -138,17 +138,25 @@ void orc_rhs(const orc_problem* p, const double* u, double* out) {
             out[n + i] = P[3] * lv + (P[1] * a - b * a2);
           } break;
           case ORC_SWE2D: {
-            /* dU/dt = -(F_{x+1/2} - F_{x-1/2})/hx - (G_{y+1/2} - G_{y-1/2})/hy */
+            /* dU/dt = -(F_{x+1/2} - F_{x-1/2})/hx - (G_{y+1/2} - G_{y-1/2})/hy
+             *         + (0, -g h b_x, -g h b_y)   (Sec. 5.3) */
             double g = P[0];
-            long ie = ((long)y) * nx + (x + 1) % nx;
-            long iw = ((long)y) * nx + (x + nx - 1) % nx;
-            long in_ = ((long)((y + 1) % ny)) * nx + x;
-            long is = ((long)((y + ny - 1) % ny)) * nx + x;
+            int wall = p->bc == ORC_BC_NEUMANN;
+            long ie = ((long)y) * nx + nbr(x, 1, nx, p->bc);
+            long iw = ((long)y) * nx + nbr(x, -1, nx, p->bc);
+            long in_ = ((long)nbr(y, 1, ny, p->bc)) * nx + x;
+            long is = ((long)nbr(y, -1, ny, p->bc)) * nx + x;
             double C[3], E[3], W[3], Nn[3], S[3];
             for (int q = 0; q < 3; ++q) {
               C[q] = u[q * n + i]; E[q] = u[q * n + ie]; W[q] = u[q * n + iw];
               Nn[q] = u[q * n + in_]; S[q] = u[q * n + is];
             }
+            /* reflecting walls: the cell across the wall is this cell with
+             * its normal momentum negated */
+            if (wall && x == nx - 1) E[1] = -E[1];
+            if (wall && x == 0) W[1] = -W[1];
+            if (wall && y == ny - 1) Nn[2] = -Nn[2];
+            if (wall && y == 0) S[2] = -S[2];
             double Fe[3], Fw[3], Gn[3], Gs[3];
             swe_flux(g, 0, C, E, Fe);
             swe_flux(g, 0, W, C, Fw);
@@ -157,6 +165,15 @@ void orc_rhs(const orc_problem* p, const double* u, double* out) {
             double ihx = 1.0 / hx, ihy = 1.0 / hy;
             for (int q = 0; q < 3; ++q)
               out[q * n + i] = (Fw[q] - Fe[q]) * ihx + (Gs[q] - Gn[q]) * ihy;
+            if (p->bathy) {
+              /* -g h grad b by central differences of b (across a wall the
+               * bottom's value is the cell's own) */
+              const double* b = p->bathy;
+              double bx = g * ((b[ie] - b[iw]) * (0.5 / hx));
+              double by = g * ((b[in_] - b[is]) * (0.5 / hy));
+              out[n + i] = out[n + i] - C[0] * bx;
+              out[2 * n + i] = out[2 * n + i] - C[0] * by;
+            }
           } break;
           default: out[i] = 0.0;
         }
@@ -562,7 +579,7 @@ int orc_solve(const orc_problem* p, const double* u0, double* U,
   const long d = orc_dim(p);
   if (N < 1 || p->nF < 1 || p->nG < 1 || p->m < 1 || p->m > 64 || M < 1 ||
       p->max_iters < 1 || p->bc < 0 || p->bc > 1 ||
-      (p->bc == ORC_BC_NEUMANN && p->pde == ORC_SWE2D))
+      (p->bathy && p->pde != ORC_SWE2D))
     return ORC_EINVAL;
   const int K_max = p->max_iters < N ? p->max_iters : N;
   /* At most N - k + 1 pairs are appended at iteration k (L >= k - 1). */

@@ -48,7 +48,11 @@ enum { ORC_CORR_RANDNET = 0, ORC_CORR_PARAREAL = 1 };
 /* Boundary: periodic, or no-flux (homogeneous Neumann) on a cell-centred
  * finite-volume grid -- the flux through a wall face is zero, i.e. the
  * neighbour across the wall is the cell itself (Sec. 5.2: no-flow
- * Neumann boundary, finite-volume discretisation). */
+ * Neumann boundary, finite-volume discretisation).  Shallow water
+ * (Sec. 5.3: a box whose walls the water rebounds from): the cell across a
+ * wall mirrors the cell with its momentum normal to the wall negated (a
+ * reflecting wall: zero normal gradient of h and of the tangential
+ * momentum, no mass through the wall). */
 enum { ORC_BC_PERIODIC = 0, ORC_BC_NEUMANN = 1 };
 enum { ORC_SCALE_MINMAX = 0, ORC_SCALE_NONE = 1 };
 /* Fine integrator: classic RK4, or RK8 = the explicit eleven-stage
@@ -75,6 +79,9 @@ typedef struct {
   int gscheme;              /* G integrator: 0 forward Euler (RK1), 1 RK4  */
   int bc;                   /* ORC_BC_* (shallow water: periodic only)     */
   int fscheme;              /* ORC_F_*: F integrator                       */
+  const double* bathy;      /* shallow water: bottom b at the nx*ny cell
+                               centres (row-major, x fastest), or NULL for a
+                               flat bottom; adds -g h grad b (Sec. 5.3)     */
 } orc_problem;
 
 typedef struct {

@@ -7,7 +7,8 @@ eigenvectors cos(pi k x_i / L) with eigenvalues -(4/h^2) sin^2(pi k h / 2L),
 k = 0..n-1 -- a mode that the periodic operator does not have for odd k.
 Pins: the RK4 / Euler closed forms of such modes (1D, 2D, 3D), exact mass
 conservation of the diffusion operator, the boundary stencil itself, the
-Burgers/advection wall differences, and the refusal for shallow water."""
+Burgers/advection wall differences.  Shallow-water walls (reflecting) are
+pinned in test_oracle_swe_box.py."""
 import math
 
 import numpy as np
@@ -121,8 +122,3 @@ def test_burgers_wall_differences(orc):
     assert r[0] == pytest.approx(exp0, rel=1e-13)
     assert r[-1] == pytest.approx(expn, rel=1e-13)
 
-
-def test_shallow_water_refuses_neumann(orc):
-    cfg = W.config("swe2d", nx=16, ny=16, N=2, nF=4, nG=2, bc="neumann")
-    rc, _, _, _ = orc.solve(orc.problem(cfg), W.initial_condition(cfg)[0])
-    assert rc == 1  # ORC_EINVAL

@@ -66,6 +66,18 @@ CONFIGS = {
                   param=[9.81], t0=0.0, tN=0.5, N=32, nF=0, nG=0, M=100, m=4,
                   lam=1e-7, tol=1e-6, batch=1, ic="gauss_bump",
                   seed=SEED_BASE + 4),
+    # The paper's radial dam break in a box (Sec. 5.3 and its appendix):
+    # [-5,5] x [0,5] (here shifted to [0,10] x [0,5]), reflecting walls, a
+    # Gaussian column at (-2.5, 1.5) with covariance 0.25 I, t in [0, 20],
+    # N = 235, G = 7 Euler steps per slice, m = 3.  Mesh 100 x 50 cells
+    # (the paper's coarsest 101 x 51 points, made even for the FP32 tiles);
+    # nF from the CFL rule of swe_steps (the paper's 1e5 RK4 steps per slice
+    # is far below the stability limit).  Flat bottom unless a
+    # ``bathymetry`` array is added.
+    "swe_box": dict(pde="swe2d", nx=100, ny=50, nz=1, lx=10.0, ly=5.0, lz=1.0,
+                    param=[9.81], t0=0.0, tN=20.0, N=235, nF=0, nG=7, M=100, m=3,
+                    lam=1e-7, tol=1e-6, batch=1, ic="gauss_column", bc="neumann",
+                    seed=SEED_BASE + 6),
 }
 
 
@@ -110,6 +122,10 @@ def initial_condition(cfg: dict, seed: int | None = None,
     * ``gauss_bump``: shallow-water depth 1 + A exp(-r^2 / (2 w^2)) around the
       domain centre (minimum-image distance), A ~ U(0.1,0.5),
       w ~ U(0.05,0.2), zero momentum.
+    * ``gauss_column``: shallow-water depth 1 plus the bivariate normal
+      density with mean (0.25 lx, 0.3 ly) and covariance 0.25 (lx / 10)^2 I
+      (the paper's column at (-2.5, 1.5), covariance 0.25 I, in a [-5, 5] x
+      [0, 5] box), at the cell centres, zero momentum; deterministic.
     * ``sine``: single Fourier mode sin(2 pi k x / lx) (test operators), mode
       number cfg['mode'] (default 1), along each axis that has > 1 point.
     * ``cos9``: u0(x) = 0.5 (cos(9 pi x / 2) + 1) on [-1, 1), the Burgers
@@ -148,6 +164,13 @@ def initial_condition(cfg: dict, seed: int | None = None,
             dy = dy - cfg["ly"] * np.round(dy / cfg["ly"])
             r2 = dy[:, None] ** 2 + dx[None, :] ** 2
             out[b, :n] = (1.0 + amp * np.exp(-r2 / (2.0 * w * w))).ravel()
+            out[b, n:] = 0.0
+        elif kind == "gauss_column":
+            var = 0.25 * (cfg["lx"] / 10.0) ** 2
+            xs = (np.arange(nx) + 0.5) / nx * cfg["lx"] - 0.25 * cfg["lx"]
+            ys = (np.arange(ny) + 0.5) / ny * cfg["ly"] - 0.3 * cfg["ly"]
+            r2 = ys[:, None] ** 2 + xs[None, :] ** 2
+            out[b, :n] = (1.0 + np.exp(-r2 / (2.0 * var)) / (2.0 * np.pi * var)).ravel()
             out[b, n:] = 0.0
         elif kind == "cos9":
             x = -1.0 + cfg["lx"] * np.arange(nx) / nx
