@@ -66,7 +66,7 @@ typedef enum {
   RNP_DIFFREACT2D = 1, /* param: Du, Dv, c   (FitzHugh-Nagumo kinetics)   */
   RNP_BRUSS2D = 2,     /* param: a, b, D0, D1                              */
   RNP_BRUSS3D = 3,     /* param: a, b, D0, D1                              */
-  RNP_SWE2D = 4,       /* param: g  (Rusanov flux, flat bottom)            */
+  RNP_SWE2D = 4,       /* param: g  (Rusanov flux; bottom: bathymetry)     */
   RNP_HEAT = 5,        /* param: D  (1, 2 or 3 dimensions)                 */
   RNP_ADVECT1D = 6     /* param: c                                         */
 } rnp_pde;
@@ -108,7 +108,10 @@ typedef enum { RNP_BC_PERIODIC = 0, RNP_BC_NEUMANN = 1 } rnp_bc;
 /* PERIODIC: every axis wraps.  NEUMANN: no-flux walls on a cell-centred
  * finite-volume grid (Sec. 5.2's no-flow Neumann boundary): the flux through
  * a wall face is zero, i.e. the neighbour across the wall is the cell
- * itself.  Shallow water accepts PERIODIC only (RNP_EINVAL otherwise). */
+ * itself.  Shallow water (Sec. 5.3: a box whose walls the water rebounds
+ * from): reflecting walls, the cell across a wall mirrors the cell with its
+ * momentum normal to the wall negated (zero normal gradient of h and of the
+ * tangential momentum, no mass through a wall). */
 
 #define RNP_MAX_BATCH 64
 #define RNP_MAX_M 32   /* largest number of nearest neighbours m */
@@ -141,6 +144,14 @@ typedef struct {
                              fastest (ignored when cluster/threads are set) */
   int bc;                 /* rnp_bc                                        */
   int fscheme;            /* rnp_fscheme                                   */
+  const double* bathymetry; /* shallow water only: HOST array of the bottom
+                             b at the nx*ny cell centres (x fastest), read
+                             during rnp_create only (the caller keeps
+                             ownership); adds -g h grad b to the momentum
+                             equations (Sec. 5.3) by central differences
+                             of b (across a wall b's neighbour is the cell
+                             itself).  NULL: flat bottom.  Non-NULL for
+                             another PDE: RNP_EINVAL.                       */
 } rnp_problem;
 
 typedef struct {

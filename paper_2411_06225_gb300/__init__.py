@@ -50,7 +50,7 @@ class Problem(C.Structure):
         ("scale_mode", C.c_int), ("gscheme", C.c_int), ("precision", C.c_int),
         ("exec_", C.c_int), ("batch", C.c_int), ("cluster", C.c_int),
         ("threads", C.c_int), ("max_pairs", C.c_longlong), ("autotune", C.c_int),
-        ("bc", C.c_int), ("fscheme", C.c_int),
+        ("bc", C.c_int), ("fscheme", C.c_int), ("bathymetry", C.POINTER(C.c_double)),
     ]
 
 
@@ -99,6 +99,14 @@ def problem(cfg: dict, precision: str = "fp64", exec: str = "fused", **kw) -> Pr
     p.autotune = int(c.get("autotune", 0))
     p.bc = {"periodic": 0, "neumann": 1}[c.get("bc", "periodic")]
     p.fscheme = {"rk4": 0, "rk8": 1}[c.get("fscheme", "rk4")]
+    b = c.get("bathymetry")
+    if b is not None:
+        import numpy as np
+        b = np.ascontiguousarray(b, dtype=np.float64).reshape(-1)
+        if b.size != c["nx"] * c["ny"] * c["nz"]:
+            raise ValueError("bathymetry needs one value per cell")
+        p._bathymetry = b                 # alive as long as the struct
+        p.bathymetry = b.ctypes.data_as(C.POINTER(C.c_double))
     return p
 
 

@@ -52,6 +52,8 @@ struct rnp_ctx {
   int* dP = nullptr;
   unsigned long long* err = nullptr;
   double* plain_work = nullptr;
+  double* bath = nullptr;         // shallow-water bottom term [2][n] (or null)
+  float* bath32 = nullptr;
   long long* d_items = nullptr;   // src, dst, soff, phioff tables (4 * itemcap)
   int* d_app = nullptr;           // b, j, p (3 * itemcap)
   int* d_gate = nullptr;          // (N + 1) * B
@@ -168,8 +170,7 @@ const char* validate(const rnp_problem* p) {
   if (p->batch < 1 || p->batch > RNP_MAX_BATCH) return "batch must be in [1, 64]";
   if (p->corr != RNP_CORR_RANDNET && p->corr != RNP_CORR_PARAREAL) return "unknown corr";
   if (p->bc != RNP_BC_PERIODIC && p->bc != RNP_BC_NEUMANN) return "unknown bc";
-  if (p->bc == RNP_BC_NEUMANN && p->pde == RNP_SWE2D)
-    return "shallow water supports periodic boundaries only";
+  if (p->bathymetry && p->pde != RNP_SWE2D) return "bathymetry applies to shallow water only";
   if (p->scale_mode != RNP_SCALE_MINMAX && p->scale_mode != RNP_SCALE_NONE)
     return "unknown scale_mode";
   if (p->gscheme != RNP_G_EULER && p->gscheme != RNP_G_RK4) return "unknown gscheme";
@@ -186,12 +187,52 @@ const char* validate(const rnp_problem* p) {
   return nullptr;
 }
 
+// Shallow water over a bottom b (Sec. 5.3): the per-cell factors of the
+// term -g h grad b, g (b_E - b_W) (1 / (2 hx)) and g (b_N - b_S) (1 / (2 hy))
+// (across a wall the bottom's neighbour is the cell itself), in FP64 and
+// rounded to FP32, on the device; the stencils read them through Coef.
+bool upload_bathymetry(rnp_ctx* c, const rnp_problem& p) {
+  const int nx = p.nx, ny = p.ny;
+  const long long n = (long long)nx * ny;
+  const double hx = p.lx / nx, hy = p.ly / ny, g = p.param[0];
+  const bool wall = p.bc == RNP_BC_NEUMANN;
+  auto nb = [&](int i, int dir, int len) {
+    const int j = i + dir;
+    if (j >= 0 && j < len) return j;
+    if (wall) return i;
+    return j < 0 ? j + len : j - len;
+  };
+  const double* b = p.bathymetry;
+  std::vector<double> hb(2 * n);
+  std::vector<float> hf(2 * n);
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      const long long i = (long long)y * nx + x;
+      hb[i] = g * ((b[(long long)y * nx + nb(x, 1, nx)] - b[(long long)y * nx + nb(x, -1, nx)]) *
+                   (0.5 / hx));
+      hb[n + i] = g * ((b[(long long)nb(y, 1, ny) * nx + x] - b[(long long)nb(y, -1, ny) * nx + x]) *
+                       (0.5 / hy));
+    }
+  for (long long i = 0; i < 2 * n; ++i) hf[i] = (float)hb[i];
+  if (dalloc(&c->bath, (size_t)(2 * n)) != cudaSuccess ||
+      dalloc(&c->bath32, (size_t)(2 * n)) != cudaSuccess)
+    return false;
+  if (cudaMemcpy(c->bath, hb.data(), sizeof(double) * 2 * n, cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemcpy(c->bath32, hf.data(), sizeof(float) * 2 * n, cudaMemcpyHostToDevice) !=
+          cudaSuccess)
+    return false;
+  c->coef.bath = c->bath;
+  c->coef.bath32 = c->bath32;
+  return true;
+}
+
 void destroy_buffers(rnp_ctx* c) {
   void* bufs[] = {c->U, c->Fv, c->Gc, c->Yv, c->gbuf, c->qbuf, c->phic, c->phiq, c->Sds,
                   c->Yds, c->Phi, c->A, c->zeta, c->sc, c->sr, c->scale_work, c->feat_part,
                   c->nn_part, c->dist, c->alpha, c->idx, c->meff, c->flags, c->dP, c->err,
                   c->plain_work, c->d_items, c->d_app, c->d_gate, c->A32, c->S32, c->q32,
-                  c->d_mask, c->Abf, c->tc_part, c->d_qsrc, c->d_qgate};
+                  c->d_mask, c->Abf, c->tc_part, c->d_qsrc, c->d_qgate, c->bath, c->bath32};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->h_items) cudaFreeHost(c->h_items);
@@ -637,6 +678,12 @@ rnp_status rnp_create(const rnp_problem* prob, void* cuda_stream, rnp_ctx** out)
       cudaStreamSynchronize(c->st) != cudaSuccess) {
     cudaGetLastError();
     return bail(RNP_ECUDA, "initialisation failed");
+  }
+  if (prob->bathymetry) {
+    if (!upload_bathymetry(c, *prob)) {
+      cudaGetLastError();
+      return bail(RNP_ENOMEM, "bathymetry upload failed");
+    }
   }
   for (int i = 0; i < B * 3; ++i) { c->h_c[i] = 0.0; c->h_r[i] = 1.0; }
   if (prob->autotune && !c->plain && prob->cluster == 0 && prob->threads == 0) {

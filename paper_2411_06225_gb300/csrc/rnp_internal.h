@@ -41,9 +41,14 @@ struct Geom {
 };
 
 // PDE constants, precomputed on the host in FP64 exactly as the plain
-// serial formulas use them (coefficients, 1/h^2, 1/(2h), 1/h).
+// serial formulas use them (coefficients, 1/h^2, 1/(2h), 1/h), and the
+// shallow-water bottom term: bath[i] = g (b_E - b_W) (1 / (2 hx)) and
+// bath[n + i] = g (b_N - b_S) (1 / (2 hy)) per cell (device, FP64; bath32
+// the same rounded to FP32), or null for a flat bottom.
 struct Coef {
   double k[12];
+  const double* bath;
+  const float* bath32;
 };
 
 // Work-item description of a stencil launch: item w reads the state at

@@ -205,7 +205,26 @@ __device__ __forceinline__ void fused_cell_rhs(const FusedParams& P, const T* B,
       if (DIMS == 2) { Nv[q] = vp; Sv[q] = vm; } else { Uv[q] = vp; Dv[q] = vm; }
     }
   }
+  if constexpr (KP == KP_SWE) {
+    // reflecting walls: the cell across a wall is this cell with its
+    // momentum normal to the wall negated
+    if (wall) {
+      if (x + 1 == nx) Ev[1] = -Ev[1];
+      if (x == 0) Wv[1] = -Wv[1];
+      if (o + 1 == nloc && rank == CS - 1) Nv[2] = -Nv[2];
+      if (o == 0 && rank == 0) Sv[2] = -Sv[2];
+    }
+  }
   rhs_point<KP, T, EX>(Cv, Ev, Wv, Nv, Sv, Uv, Dv, kk, k);
+  if constexpr (KP == KP_SWE) {
+    // bottom term -g h grad b
+    if (P.coef.bath) {
+      using A = Ar<T, EX>;
+      const long long gi = (long long)rank * ncell + c;
+      k[1] = A::sub(k[1], A::mul(Cv[0], T(P.coef.bath[gi])));
+      k[2] = A::sub(k[2], A::mul(Cv[0], T(P.coef.bath[P.n + gi])));
+    }
+  }
 }
 
 template <int KP, typename T, bool EX, int R>
@@ -479,8 +498,23 @@ __global__ void k_stage_plain(const PlainParams P) {
       Uv[q] = DIMS >= 3 ? Wq[at(x, y, zu)] : 0.0;
       Dv[q] = DIMS >= 3 ? Wq[at(x, y, zd)] : 0.0;
     }
+    if constexpr (KP == KP_SWE) {
+      // reflecting walls: the normal momentum of the mirrored cell is negated
+      if (wall) {
+        if (x + 1 == nx) Ev[1] = -Ev[1];
+        if (x == 0) Wv[1] = -Wv[1];
+        if (y + 1 == ny) Nv[2] = -Nv[2];
+        if (y == 0) Sv[2] = -Sv[2];
+      }
+    }
     double k[NC];
     rhs_point<KP, double, true>(Cv, Ev, Wv, Nv, Sv, Uv, Dv, P.coef.k, k);
+    if constexpr (KP == KP_SWE) {
+      if (P.coef.bath) {   // bottom term -g h grad b
+        k[1] = A::sub(k[1], A::mul(Cv[0], P.coef.bath[cell]));
+        k[2] = A::sub(k[2], A::mul(Cv[0], P.coef.bath[P.n + cell]));
+      }
+    }
     for (int q = 0; q < NC; ++q) {
       const long long e = (long long)item * P.d + q * P.n + cell;
       double w;
@@ -674,6 +708,26 @@ __device__ __forceinline__ void push_edge(const HaloOut& h, bool to_prev, uint32
   else st_async_vec<PX>(a, v, mb + h.moff);
 }
 
+// push_edge for component q; a shallow-water wall ghost row (a local target
+// when WALL) mirrors the row with its normal momentum hv negated
+template <int KP, int PX, bool WALL>
+__device__ __forceinline__ void push_edge_q(const HaloOut& h, bool to_prev, uint32_t elem,
+                                            const float* v, int q) {
+  if constexpr (WALL && KP == KP_SWE) {
+    if (q == 2) {
+      const uint4 t = *h.tab;
+      if (h.self || (to_prev ? t.z : t.w) == 0) {
+        float nv[PX];
+#pragma unroll
+        for (int p = 0; p < PX; ++p) nv[p] = -v[p];
+        push_edge<PX>(h, to_prev, elem, nv);
+        return;
+      }
+    }
+  }
+  push_edge<PX>(h, to_prev, elem, v);
+}
+
 template <int KP, int PX, int RS, int STAGE, bool XS, bool WALL>
 __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* __restrict__ B,
                                             float* __restrict__ Bn, float* ulo,
@@ -682,7 +736,8 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
                                             int ncell, int plane, int nloc, int ofirst, int dir,
                                             int rowoff, int woff, int eoff, int yn_off, int ys_off,
                                             bool euler, const HaloOut& ho, unsigned xmask,
-                                            int xw, int xwest, int xeast, bool xlo, bool xhi) {
+                                            int xw, int xwest, int xeast, bool xlo, bool xhi,
+                                            const float* __restrict__ bth) {
   const float* kk = P.kf;
   const float dt = P.fdt, h2 = P.fh2, h6 = P.fh6;
   constexpr int NC = KT<KP>::NC, DIMS = KT<KP>::DIMS;
@@ -729,12 +784,22 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
       }
       if constexpr (WALL) {
         // no-flux walls: the neighbour across the wall is the cell itself
-        if (xlo) ew[q] = cur[q][0];
-        if (xhi) ee[q] = cur[q][PX - 1];
+        // (shallow water: with its normal momentum hu negated)
+        constexpr bool kFlip = KP == KP_SWE;
+        if (xlo) ew[q] = (kFlip && q == 1) ? -cur[q][0] : cur[q][0];
+        if (xhi) ee[q] = (kFlip && q == 1) ? -cur[q][PX - 1] : cur[q][PX - 1];
       }
       if (DIMS == 3) {
         ld_vec<PX>(Bq + yn_off, yn[q]);
         ld_vec<PX>(Bq + ys_off, ys[q]);
+      }
+    }
+    // shallow water: the bottom term's per-cell factors of this tile row
+    float bx[PX], by[PX];
+    if constexpr (KP == KP_SWE) {
+      if (bth) {
+        ld_vec<PX>(bth + cb, bx);
+        ld_vec<PX>(bth + P.n + cb, by);
       }
     }
     float wout[NC][PX];
@@ -754,6 +819,12 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
         else { Nv[q] = Sv[q] = Uv[q] = Dv[q] = 0.f; }
       }
       rhs_point<KP, float, false>(Cv, Ev, Wv, Nv, Sv, Uv, Dv, kk, k);
+      if constexpr (KP == KP_SWE) {
+        if (bth) {
+          k[1] = k[1] - Cv[0] * bx[p];
+          k[2] = k[2] - Cv[0] * by[p];
+        }
+      }
 #pragma unroll
       for (int q = 0; q < NC; ++q) {
         float w;
@@ -788,9 +859,9 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
         // edge rows are visited first: row 0 (walking up) or nloc - 1 (down);
         // a CTA with a single row group also sends its last row at r = RS - 1
         if (r == 0 && ho.on && ho.edge)
-          push_edge<PX>(ho, ho.first, q * ncell + rowoff, wout[q]);
+          push_edge_q<KP, PX, WALL>(ho, ho.first, q * ncell + rowoff, wout[q], q);
         if (r == RS - 1 && ho.on && ho.first && ho.last)
-          push_edge<PX>(ho, false, q * ncell + rowoff, wout[q]);
+          push_edge_q<KP, PX, WALL>(ho, false, q * ncell + rowoff, wout[q], q);
 #pragma unroll
         for (int p = 0; p < PX; ++p) { back[q][p] = cur[q][p]; cur[q][p] = ahead[q][p]; }
       }
@@ -899,6 +970,9 @@ __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant_
 
   const long long base = (long long)rank * nloc * plane;
   const double* in = P.in + item_off(P.it.src_off, P.it.src_base, P.it.src_stride, item) + base;
+  // shallow water over a bottom b: this CTA's rows of the bottom term
+  const float* const bth =
+      (KP == KP_SWE && P.coef.bath32) ? P.coef.bath32 + base : nullptr;
   float uh[RS][NC][PX], acc[RS][NC][PX];
 #pragma unroll
   for (int r = 0; r < RS; ++r)
@@ -930,8 +1004,8 @@ __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant_
         v0[p] = dir > 0 ? uh[0][q][p] : uh[RS - 1][q][p];
         v1[p] = dir > 0 ? uh[RS - 1][q][p] : uh[0][q][p];
       }
-      if (first) push_edge<PX>(h0, true, q * ncell + rowoff, v0);
-      if (last) push_edge<PX>(h0, false, q * ncell + rowoff, v1);
+      if (first) push_edge_q<KP, PX, WALL>(h0, true, q * ncell + rowoff, v0, q);
+      if (last) push_edge_q<KP, PX, WALL>(h0, false, q * ncell + rowoff, v1, q);
     }
   }
 
@@ -962,7 +1036,7 @@ __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant_
   mixed_stage<KP, PX, RS, STG, XS, WALL>(P, BIN, BOUT, ulo, uh, acc, ncell, plane, nloc,      \
                                          ofirst, dir, rowoff, woff, eoff, yn_off, ys_off,    \
                                          EUL, halo_out((PAR) ^ 1, ON), xmask, xsw, xwest,    \
-                                         xeast, xlo, xhi)
+                                         xeast, xlo, xhi, bth)
 
   __syncthreads();
   for (int step = 0; step < P.steps; ++step) {
@@ -1037,10 +1111,9 @@ inline FusedFn fused_rk8_for_R(int R) {
 // beyond use and are not instantiated (the host picker never asks for them).
 static constexpr int kMaxTileValues = 40;
 
-// Shallow water has periodic boundaries only: no wall instantiations.
 template <int KP, int PX, int RS, bool XS, bool WALL, bool RK>
 inline FusedFn mixed_if_fits() {
-  if constexpr (RS * KT<KP>::NC * PX <= kMaxTileValues && !(WALL && KP == KP_SWE))
+  if constexpr (RS * KT<KP>::NC * PX <= kMaxTileValues)
     return k_stencil_mixed<KP, PX, RS, XS, WALL, RK>;
   else
     return nullptr;
@@ -1091,6 +1164,32 @@ RNP_STENCIL_DECL(bruss2)
 RNP_STENCIL_DECL(bruss3)
 RNP_STENCIL_DECL(swe)
 #undef RNP_STENCIL_DECL
+
+template <int KP, bool WALL>
+inline FusedFn mixed_for_w(int PX, int RS, bool XS, bool RK) {
+  if (PX == 2) return RK ? mixed_for_xs<KP, 2, WALL, true>(RS, XS) : mixed_for_xs<KP, 2, WALL, false>(RS, XS);
+  if (PX == 4) return RK ? mixed_for_xs<KP, 4, WALL, true>(RS, XS) : mixed_for_xs<KP, 4, WALL, false>(RS, XS);
+  return nullptr;
+}
+
+// Shallow water compiles its wall instantiations of the mixed kernel in a
+// translation unit of their own (stencil_swe_wall.cu) so the two halves
+// build in parallel.
+FusedFn mixed_fn_swe_wall(int PX, int RS, bool XS, bool RK);
+
+#define RNP_STENCIL_DEFINE_SPLIT(KPV, NAME)                                          \
+  FusedFn fused_fn_##NAME(int R) { return fused_for_R<KPV, double, true>(R); }       \
+  FusedFn fused_rk8_fn_##NAME(int R) { return fused_rk8_for_R<KPV>(R); }             \
+  FusedFn mixed_fn_##NAME(int PX, int RS, bool XS, bool WALL, bool RK) {             \
+    return WALL ? mixed_fn_##NAME##_wall(PX, RS, XS, RK)                             \
+                : mixed_for_w<KPV, false>(PX, RS, XS, RK);                           \
+  }                                                                                  \
+  PlainFn plain_fn_##NAME() { return k_stage_plain<KPV>; }
+
+#define RNP_STENCIL_DEFINE_WALL(KPV, NAME)                                           \
+  FusedFn mixed_fn_##NAME##_wall(int PX, int RS, bool XS, bool RK) {                 \
+    return mixed_for_w<KPV, true>(PX, RS, XS, RK);                                   \
+  }
 
 #define RNP_STENCIL_DEFINE(KPV, NAME)                                                \
   FusedFn fused_fn_##NAME(int R) { return fused_for_R<KPV, double, true>(R); }       \

@@ -3,5 +3,5 @@
 #include "stencil_impl.cuh"
 
 namespace rnp {
-RNP_STENCIL_DEFINE(KP_SWE, swe)
+RNP_STENCIL_DEFINE_SPLIT(KP_SWE, swe)
 }  // namespace rnp

@@ -35,8 +35,11 @@ CLASS_KEYS = ("pde", "nx", "ny", "nz", "lx", "ly", "lz", "t0", "tN", "N", "nF", 
 
 
 def class_key(cfg: dict) -> tuple:
-    """Requests with equal keys share a pooled context."""
-    return tuple(cfg.get(k) for k in CLASS_KEYS) + (tuple(cfg["param"]),)
+    """Requests with equal keys share a pooled context (a bottom profile is
+    part of the class: it is fixed per context)."""
+    b = cfg.get("bathymetry")
+    bkey = None if b is None else np.ascontiguousarray(b, np.float64).tobytes()
+    return tuple(cfg.get(k) for k in CLASS_KEYS) + (tuple(cfg["param"]), bkey)
 
 
 def pool_bytes(cfg: dict, slots: int, precision: str) -> int:

@@ -123,9 +123,3 @@ def test_solve_against_oracle(R, orc, precision):
         assert abs(st["K"] - so.K) <= 1
         assert rel(U, Uo) <= 1e-5
 
-
-def test_shallow_water_refuses_neumann(R):
-    cfg = W.config("swe2d", nx=32, ny=32, N=2, nF=8, nG=4, bc="neumann")
-    with pytest.raises(R.RnpError) as e:
-        R.Solver(R.problem(cfg))
-    assert e.value.status == R.RNP_EINVAL
