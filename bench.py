@@ -52,10 +52,14 @@ UNIT = "cell-updates/s"
 #   diffusion-reaction 2D: per grid point and stage 16 (u) + 12 (v)
 #   Brusselator 2D: 16 (u) + 13 (v); 3D: 21 (u) + 18 (v)
 #   Burgers 1D: 9 per point and stage
+#   shallow water: 39 per Rusanov face (4 divisions, 2 square roots, the
+#   two physical fluxes, speeds, the maximum, 3 x 5 for the face flux) x 4
+#   faces + 15 for the flux differences = 171 per grid point and stage
 FLOPS_PER_CELL_UPDATE = {"diffreact2d": (4 * (16 + 12) + 2 * 13) / 2.0,
                          "bruss2d": (4 * (16 + 13) + 2 * 13) / 2.0,
                          "bruss3d": (4 * (21 + 18) + 2 * 13) / 2.0,
-                         "burgers1d": 4 * 9 + 13.0}
+                         "burgers1d": 4 * 9 + 13.0,
+                         "swe_box": (4 * 171 + 3 * 13) / 3.0}
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one fine launch
@@ -148,8 +152,10 @@ def dist_env():
 
 def describe(cfg: dict) -> str:
     grid = "x".join(str(v) for v in (cfg["nx"], cfg["ny"], cfg["nz"]) if v > 1)
-    return (f"{cfg['pde']} {grid}x{W.ncomp(cfg)} periodic, N={cfg['N']}, "
-            f"F=RK4x{cfg['nF']}, G=Eulerx{cfg['nG']}, M={cfg['M']}, m={cfg['m']}, "
+    bc = "walls" if cfg.get("bc", "periodic") == "neumann" else "periodic"
+    fs = cfg.get("fscheme", "rk4").upper()
+    return (f"{cfg['pde']} {grid}x{W.ncomp(cfg)} {bc}, N={cfg['N']}, "
+            f"F={fs}x{cfg['nF']}, G=Eulerx{cfg['nG']}, M={cfg['M']}, m={cfg['m']}, "
             f"tol={cfg['tol']}, batch={cfg.get('batch', 1)}, max_iters={cfg['max_iters']}")
 
 
@@ -178,17 +184,19 @@ def cpu_baseline(seconds_hint: float = 20.0) -> dict:
     import oracle
     cores = os.cpu_count() or 1
     oracle.set_threads(cores)
-    cfg = W.config(WORKLOAD, nF=40)
+    full = W.config(WORKLOAD)
+    cfg = W.config(WORKLOAD, nF=min(40, full["nF"]))
     p = oracle.problem(cfg)
     u0 = W.initial_condition(cfg)[0]
     t0 = time.perf_counter()
     rc, U, st, _ = oracle.solve(p, u0)
     dt = time.perf_counter() - t0
+    grid = "x".join(str(v) for v in (cfg["nx"], cfg["ny"], cfg["nz"]) if v > 1)
     return {"value": st.fine_cell_updates / dt, "unit": UNIT, "cores": cores,
             "kind": "oracle",
-            "sample": (f"{WORKLOAD} 128x128x2, N=64, nF=40 of 2000 RK4 steps per slice, "
-                       f"full solve K={st.K} in {dt:.2f} s, FP64, slice-parallel over "
-                       f"{cores} threads")}
+            "sample": (f"{WORKLOAD} {grid}x{W.ncomp(cfg)}, N={cfg['N']}, nF={cfg['nF']} of "
+                       f"{full['nF']} RK4 steps per slice, full solve K={st.K} in {dt:.2f} s, "
+                       f"FP64, slice-parallel over {cores} threads")}
 
 
 def run_reference(args):
@@ -420,7 +428,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=["diffreact2d", "burgers1d", "bruss2d", "bruss3d"])
+                    choices=["diffreact2d", "burgers1d", "bruss2d", "bruss3d", "swe_box"])
     ap.add_argument("--max-iters", type=int, default=0)
     ap.add_argument("--tile", default="",
                     help="fixed stencil tiling 'cluster,threads' instead of the autotuner's")
