@@ -581,32 +581,86 @@ __global__ void __launch_bounds__(256) k_topm_ridge(const TP* part, int nch,
   double* pq = phiq + (long long)b * phiq_bstride;
   // Distances first (their partial loads are issued before the feature
   // partials', so both are in flight together): four interleaved partial
-  // sums over the chunks, then combined.  A thread keeps the keys of its
-  // first kKeys candidates (p = threadIdx.x + t * 256) in registers.
-  constexpr int kKeys = 4;
-  unsigned long long mykey[kKeys];
-  double* db = dist + (long long)b * cap;
+  // sums over the chunks, then combined; two stored rows per iteration
+  // (p and p + 256) so that twice the loads are in flight.  Each thread
+  // keeps its kTop best (distance key, index) pairs in a sorted register
+  // list (insertion by compare-and-swap with static indices; candidates
+  // arrive in increasing index, so a strict comparison keeps the lower
+  // index first among equal keys).
+  constexpr int kTop = 8;
+  const bool in_regs = me <= kTop;
+  unsigned long long tk[kTop];
+  unsigned ti[kTop];
 #pragma unroll
-  for (int t = 0; t < kKeys; ++t) mykey[t] = ~0ULL;
+  for (int t = 0; t < kTop; ++t) { tk[t] = ~0ULL; ti[t] = 0xffffffffu; }
+  auto insert = [&](unsigned long long k, unsigned i) {
+#pragma unroll
+    for (int t = 0; t < kTop; ++t) {
+      const bool lt = k < tk[t];
+      const unsigned long long ok = tk[t];
+      const unsigned oi = ti[t];
+      tk[t] = lt ? k : ok;
+      ti[t] = lt ? i : oi;
+      k = lt ? ok : k;
+      i = lt ? oi : i;
+    }
+  };
+  double* db = dist + (long long)b * cap;
   const int B = gridDim.x;                          // members (one CTA each)
   const long long cstride = (long long)B * cap;     // chunk k of row p at pp[k * cstride]
-  for (int p = threadIdx.x, t = 0; p < P; p += blockDim.x, ++t) {
-    const TP* pp = part + (long long)b * cap + p;
-    TP a0 = TP(0), a1 = TP(0), a2 = TP(0), a3 = TP(0);
-    int k = 0;
+  if (P <= (int)blockDim.x) {
+    // one stored row per thread: its key starts the (otherwise empty) list
+    const int p = threadIdx.x;
+    if (p < P) {
+      const TP* pa = part + (long long)b * cap + p;
+      TP a0 = TP(0), a1 = TP(0), a2 = TP(0), a3 = TP(0);
+      int k = 0;
 #pragma unroll 4
-    for (; k + 3 < nch; k += 4) {
-      a0 = a0 + pp[k * cstride];
-      a1 = a1 + pp[(k + 1) * cstride];
-      a2 = a2 + pp[(k + 2) * cstride];
-      a3 = a3 + pp[(k + 3) * cstride];
+      for (; k + 3 < nch; k += 4) {
+        a0 = a0 + pa[k * cstride];
+        a1 = a1 + pa[(k + 1) * cstride];
+        a2 = a2 + pa[(k + 2) * cstride];
+        a3 = a3 + pa[(k + 3) * cstride];
+      }
+      for (; k < nch; ++k) a0 = a0 + pa[k * cstride];
+      const double d0 = (double)((a0 + a1) + (a2 + a3));
+      db[p] = d0;
+      tk[0] = (unsigned long long)__double_as_longlong(d0);
+      ti[0] = (unsigned)p;
     }
-    for (; k < nch; ++k) a0 = a0 + pp[k * cstride];
-    const double dv = (double)((a0 + a1) + (a2 + a3));
-    db[p] = dv;
-#pragma unroll
-    for (int u = 0; u < kKeys; ++u)
-      if (u == t) mykey[u] = (unsigned long long)__double_as_longlong(dv);
+  } else {
+    for (int p0 = threadIdx.x; p0 < P; p0 += 2 * blockDim.x) {
+      const int p1 = p0 + blockDim.x;
+      const bool two = p1 < P;
+      const TP* pa = part + (long long)b * cap + p0;
+      const TP* pb = part + (long long)b * cap + (two ? p1 : p0);
+      TP a0 = TP(0), a1 = TP(0), a2 = TP(0), a3 = TP(0);
+      TP c0 = TP(0), c1 = TP(0), c2 = TP(0), c3 = TP(0);
+      int k = 0;
+#pragma unroll 2
+      for (; k + 3 < nch; k += 4) {
+        a0 = a0 + pa[k * cstride];
+        a1 = a1 + pa[(k + 1) * cstride];
+        a2 = a2 + pa[(k + 2) * cstride];
+        a3 = a3 + pa[(k + 3) * cstride];
+        c0 = c0 + pb[k * cstride];
+        c1 = c1 + pb[(k + 1) * cstride];
+        c2 = c2 + pb[(k + 2) * cstride];
+        c3 = c3 + pb[(k + 3) * cstride];
+      }
+      for (; k < nch; ++k) {
+        a0 = a0 + pa[k * cstride];
+        c0 = c0 + pb[k * cstride];
+      }
+      const double d0 = (double)((a0 + a1) + (a2 + a3));
+      db[p0] = d0;
+      if (in_regs) insert((unsigned long long)__double_as_longlong(d0), (unsigned)p0);
+      if (two) {
+        const double d1 = (double)((c0 + c1) + (c2 + c3));
+        db[p1] = d1;
+        if (in_regs) insert((unsigned long long)__double_as_longlong(d1), (unsigned)p1);
+      }
+    }
   }
   // query features (when their partials are given): the chunk partials in
   // chunk order, + zeta, ReLU
@@ -621,35 +675,25 @@ __global__ void __launch_bounds__(256) k_topm_ridge(const TP* part, int nch,
     }
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (P <= kKeys * (int)blockDim.x) {
-    // m nearest with the keys in registers: each warp takes its me best
-    // (the winning lane drops its key), then warp 0 takes the me best of
+  if (in_regs) {
+    // m nearest from the register lists: each warp takes its me best (the
+    // winning lane pops its list head), then warp 0 takes the me best of
     // those
     for (int r = 0; r < me; ++r) {
-      unsigned long long bk = ~0ULL;
-      unsigned bi = 0xffffffffu;
-      int bt = -1;
-#pragma unroll
-      for (int t = 0; t < kKeys; ++t) {
-        const unsigned p = (unsigned)(threadIdx.x + t * blockDim.x);
-        if (mykey[t] < bk || (mykey[t] == bk && mykey[t] != ~0ULL && p < bi)) {
-          bk = mykey[t]; bi = p; bt = t;
-        }
-      }
-      if (bk == ~0ULL) { bi = 0xffffffffu; bt = -1; }
       unsigned long long wkey;
       unsigned widx;
-      warp_min_key(bk, bi, &wkey, &widx);
-      if (bt >= 0 && bi == widx) {
+      warp_min_key(tk[0], ti[0], &wkey, &widx);
+      if (widx != 0xffffffffu && ti[0] == widx) {
 #pragma unroll
-        for (int t = 0; t < kKeys; ++t)
-          if (t == bt) mykey[t] = ~0ULL;
+        for (int t = 0; t + 1 < kTop; ++t) { tk[t] = tk[t + 1]; ti[t] = ti[t + 1]; }
+        tk[kTop - 1] = ~0ULL;
+        ti[kTop - 1] = 0xffffffffu;
       }
       if (lane == 0) { ck[warp * RNP_MAX_M + r] = wkey; ci[warp * RNP_MAX_M + r] = widx; }
     }
   } else {
-    // more candidates than register slots: the same selection reading the
-    // distances back, with the warp's picks as the taken list
+    // more neighbours than the register lists hold: the same selection
+    // reading the distances back, with the warp's picks as the taken list
     __syncthreads();
     for (int r = 0; r < me; ++r) {
       unsigned long long bk = ~0ULL;

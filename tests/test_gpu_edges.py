@@ -99,3 +99,47 @@ def test_odd_grid_solve(R, orc, precision):
         U = host(U)[0]
     assert abs(st["K"] - so.K) <= (0 if precision == "fp64" else 1)
     assert rel(U, Uo) <= (1e-10 if precision == "fp64" else 1e-5)
+
+
+@pytest.mark.parametrize("P,m", [(300, 4), (1100, 4), (2600, 3), (2600, 8), (2600, 9)])
+def test_predict_large_dataset_ties_match_oracle(R, orc, P, m):
+    """The m-nearest selection over more stored rows than the selecting CTA
+    has threads (up to ten rows per thread), with the register lists (m <= 8)
+    and past them (m = 9).  Five exact copies of the query's nearest input,
+    spread over the dataset, tie at the m-th place: the lower indices win
+    (App. B's order statistics, ties by index, as in the oracle), and the
+    copies carry different targets, so a wrong pick changes the
+    prediction."""
+    cfg = W.config("diffreact2d", nx=8, ny=8, M=40, m=m)
+    p = orc.problem(cfg)
+    d = W.dim(cfg)
+    rng = np.random.default_rng(P + m)
+    Uin = rng.standard_normal((1, P, d))
+    Y = rng.standard_normal((1, P, d))
+    copies = [10, P // 3, P // 2, (3 * P) // 4, P - 1]
+    for k in copies[1:]:
+        Uin[0, k] = Uin[0, copies[0]]
+    q = Uin[:, copies[0]] + 1e-3 * rng.standard_normal((1, d))
+    c = np.array([[0.0, 0.0, 0.0]])
+    r = np.array([[1.0, 1.0, 1.0]])
+    A, z = orc.weights(p)
+    with R.Solver(R.problem(cfg, max_pairs=P)) as s:
+        s.set_scaling(c, r)
+        s.randnet_fit(dev(Uin), dev(Y))
+        out = host(s.randnet_predict(dev(q)))[0]
+    S = np.stack([orc.scale(p, c[0], r[0], u) for u in Uin[0]])
+    Phi = np.stack([orc.features(A, z, sr) for sr in S])
+    rc, ref, nn = orc.predict(p, S, Y[0], Phi, A, z, c[0], r[0], q[0])
+    assert rc >= 0
+    assert sorted(nn[:min(m, 5)]) == copies[:min(m, 5)]
+    # Identical feature rows make the Gram matrix singular up to lambda, so
+    # the features' last-bit differences (their sums run in another order
+    # on the GPU) reach the prediction amplified ~1/lambda: about 1e-5 here.
+    assert rel(out, ref) < 1e-4, rel(out, ref)
+    if m < 5:
+        # the prediction a wrong tie-break would give (the last copy instead
+        # of the first) is far outside that bound
+        perm = np.arange(P)
+        perm[[copies[0], copies[-1]]] = perm[[copies[-1], copies[0]]]
+        _, wrong, _ = orc.predict(p, S[perm], Y[0][perm], Phi[perm], A, z, c[0], r[0], q[0])
+        assert rel(wrong, ref) > 1e-2, rel(wrong, ref)
