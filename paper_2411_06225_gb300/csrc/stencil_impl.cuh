@@ -611,6 +611,27 @@ __device__ __forceinline__ void two_sum_acc(float& uh, float& ul, float x) {
   uh = h;
 }
 
+// Packed FP32 (two lanes per instruction, sm_100 and later): the two
+// x-points of a PX = 2 tile share each arithmetic instruction.  a - b is
+// fma(b, -1, a): b * -1 is exact, so the result is a - b rounded once.
+__device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 pk1(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+// two_sum_acc on both lanes
+__device__ __forceinline__ void two_sum_acc2(float2& uh, float2& ul, float2 x) {
+  const float2 s = add2(uh, x);
+  const float2 err = sub2(x, sub2(s, uh));
+  const float2 l = add2(ul, err);
+  const float2 h = add2(s, l);
+  ul = sub2(l, sub2(h, s));
+  uh = h;
+}
+
 // --- distributed-shared-memory halo exchange ------------------------------
 // Bound of a halo wait: kPolls polls (each may suspend the thread for the
 // hardware's own short time limit; a suspend-time hint would cost the
@@ -742,6 +763,8 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
   const float dt = P.fdt, h2 = P.fh2, h6 = P.fh6;
   constexpr int NC = KT<KP>::NC, DIMS = KT<KP>::DIMS;
   const int ncl = P.mcl;  // component stride of the low words (no ghost rows)
+  // diffusion-reaction with two x-points per thread: packed FP32
+  constexpr bool kPacked = PX == 2 && KP == KP_DIFFREACT;
   // Only the shallow-water fluxes tell the two outer neighbours apart; the
   // other right-hand sides take their sum.
   constexpr bool kOrdered = KP == KP_SWE;
@@ -773,6 +796,11 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
         // a width-xw shuffle wraps periodically in x
         ew[q] = __shfl_sync(xmask, cur[q][PX - 1], xwest, xw);
         ee[q] = __shfl_sync(xmask, cur[q][0], xeast, xw);
+      } else if constexpr (kPacked) {
+        // x neighbours: the adjacent tiles' edge values, loaded as scalars
+        // into one register pair for the packed arithmetic
+        ew[q] = Bq[woff + PX - 1];
+        ee[q] = Bq[eoff];
       } else {
         // x neighbours: aligned vector loads of the adjacent tiles (lanes
         // read consecutive vectors, so there is no bank conflict); keep the edge
@@ -803,53 +831,101 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
       }
     }
     float wout[NC][PX];
-#pragma unroll
-    for (int p = 0; p < PX; ++p) {
-      float Cv[NC], Ev[NC], Wv[NC], Nv[NC], Sv[NC], Uv[NC], Dv[NC], k[NC];
-#pragma unroll
-      for (int q = 0; q < NC; ++q) {
-        // outer neighbours o + 1 and o - 1
-        const float hi = kOrdered ? (dir > 0 ? ahead[q][p] : back[q][p]) : ahead[q][p];
-        const float lo = kOrdered ? (dir > 0 ? back[q][p] : ahead[q][p]) : back[q][p];
-        Cv[q] = cur[q][p];
-        Ev[q] = (p + 1 < PX) ? cur[q][p + 1] : ee[q];
-        Wv[q] = (p > 0) ? cur[q][p - 1] : ew[q];
-        if (DIMS == 2) { Nv[q] = hi; Sv[q] = lo; Uv[q] = Dv[q] = 0.f; }
-        else if (DIMS == 3) { Nv[q] = yn[q][p]; Sv[q] = ys[q][p]; Uv[q] = hi; Dv[q] = lo; }
-        else { Nv[q] = Sv[q] = Uv[q] = Dv[q] = 0.f; }
-      }
-      rhs_point<KP, float, false>(Cv, Ev, Wv, Nv, Sv, Uv, Dv, kk, k);
-      if constexpr (KP == KP_SWE) {
-        if (bth) {
-          k[1] = k[1] - Cv[0] * bx[p];
-          k[2] = k[2] - Cv[0] * by[p];
-        }
-      }
+    if constexpr (kPacked) {
+      // both x-points of the tile in packed FP32: the outer neighbours pair
+      // up as loaded; in x, point 0's east neighbour is point 1 and point
+      // 1's west neighbour point 0, the other two the adjacent tiles' edges
+      float2 kq[NC], Cq[NC], lq[NC];
 #pragma unroll
       for (int q = 0; q < NC; ++q) {
-        float w;
+        const float2 C = pk(cur[q][0], cur[q][1]);
+        // E + W of both points, as two scalar adds that write the pair
+        const float2 EW = pk(cur[q][1] + ew[q], cur[q][0] + ee[q]);
+        const float2 NS = add2(pk(ahead[q][0], ahead[q][1]), pk(back[q][0], back[q][1]));
+        const float2 lx = mul2(fma2(pk1(-2.f), C, EW), pk1(kk[3]));
+        lq[q] = fma2(fma2(pk1(-2.f), C, NS), pk1(kk[4]), lx);
+        Cq[q] = C;
+      }
+      // Du lap u + (u - u^3 - c - v);  Dv lap v + (u - v)
+      const float2 a = Cq[0], b = Cq[1];
+      const float2 a3 = mul2(mul2(a, a), a);
+      kq[0] = fma2(pk1(kk[0]), lq[0], sub2(sub2(sub2(a, a3), pk1(kk[2])), b));
+      kq[1] = fma2(pk1(kk[1]), lq[1], sub2(a, b));
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        float2 U = pk(uh[r][q][0], uh[r][q][1]);
+        float2 w;
         if (euler) {
-          float l = ulo[q * ncl + cb + p];
-          two_sum_acc(uh[r][q][p], l, __fmul_rn(dt, k[q]));
-          ulo[q * ncl + cb + p] = l;
-          w = uh[r][q][p];
+          float2 l = *reinterpret_cast<const float2*>(ulo + q * ncl + cb);
+          two_sum_acc2(U, l, mul2(pk1(dt), kq[q]));
+          *reinterpret_cast<float2*>(ulo + q * ncl + cb) = l;
+          w = U;
         } else if (STAGE == 0) {
-          acc[r][q][p] = k[q];
-          w = uh[r][q][p] + h2 * k[q];
-        } else if (STAGE == 1) {
-          acc[r][q][p] = acc[r][q][p] + 2.f * k[q];
-          w = uh[r][q][p] + h2 * k[q];
-        } else if (STAGE == 2) {
-          acc[r][q][p] = acc[r][q][p] + 2.f * k[q];
-          w = uh[r][q][p] + dt * k[q];
+          acc[r][q][0] = kq[q].x; acc[r][q][1] = kq[q].y;
+          w = fma2(pk1(h2), kq[q], U);
+        } else if (STAGE == 1 || STAGE == 2) {
+          const float2 A2 = fma2(pk1(2.f), kq[q], pk(acc[r][q][0], acc[r][q][1]));
+          acc[r][q][0] = A2.x; acc[r][q][1] = A2.y;
+          w = fma2(pk1(STAGE == 1 ? h2 : dt), kq[q], U);
         } else {
-          const float a = acc[r][q][p] + k[q];
-          float l = ulo[q * ncl + cb + p];
-          two_sum_acc(uh[r][q][p], l, __fmul_rn(h6, a));
-          ulo[q * ncl + cb + p] = l;
-          w = uh[r][q][p];
+          const float2 A2 = add2(pk(acc[r][q][0], acc[r][q][1]), kq[q]);
+          float2 l = *reinterpret_cast<const float2*>(ulo + q * ncl + cb);
+          two_sum_acc2(U, l, mul2(pk1(h6), A2));
+          *reinterpret_cast<float2*>(ulo + q * ncl + cb) = l;
+          w = U;
         }
-        wout[q][p] = w;
+        uh[r][q][0] = U.x; uh[r][q][1] = U.y;
+        wout[q][0] = w.x; wout[q][1] = w.y;
+      }
+    } else {
+#pragma unroll
+      for (int p = 0; p < PX; ++p) {
+        float Cv[NC], Ev[NC], Wv[NC], Nv[NC], Sv[NC], Uv[NC], Dv[NC], k[NC];
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+          // outer neighbours o + 1 and o - 1
+          const float hi = kOrdered ? (dir > 0 ? ahead[q][p] : back[q][p]) : ahead[q][p];
+          const float lo = kOrdered ? (dir > 0 ? back[q][p] : ahead[q][p]) : back[q][p];
+          Cv[q] = cur[q][p];
+          Ev[q] = (p + 1 < PX) ? cur[q][p + 1] : ee[q];
+          Wv[q] = (p > 0) ? cur[q][p - 1] : ew[q];
+          if (DIMS == 2) { Nv[q] = hi; Sv[q] = lo; Uv[q] = Dv[q] = 0.f; }
+          else if (DIMS == 3) { Nv[q] = yn[q][p]; Sv[q] = ys[q][p]; Uv[q] = hi; Dv[q] = lo; }
+          else { Nv[q] = Sv[q] = Uv[q] = Dv[q] = 0.f; }
+        }
+        rhs_point<KP, float, false>(Cv, Ev, Wv, Nv, Sv, Uv, Dv, kk, k);
+        if constexpr (KP == KP_SWE) {
+          if (bth) {
+            k[1] = k[1] - Cv[0] * bx[p];
+            k[2] = k[2] - Cv[0] * by[p];
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+          float w;
+          if (euler) {
+            float l = ulo[q * ncl + cb + p];
+            two_sum_acc(uh[r][q][p], l, __fmul_rn(dt, k[q]));
+            ulo[q * ncl + cb + p] = l;
+            w = uh[r][q][p];
+          } else if (STAGE == 0) {
+            acc[r][q][p] = k[q];
+            w = uh[r][q][p] + h2 * k[q];
+          } else if (STAGE == 1) {
+            acc[r][q][p] = acc[r][q][p] + 2.f * k[q];
+            w = uh[r][q][p] + h2 * k[q];
+          } else if (STAGE == 2) {
+            acc[r][q][p] = acc[r][q][p] + 2.f * k[q];
+            w = uh[r][q][p] + dt * k[q];
+          } else {
+            const float a = acc[r][q][p] + k[q];
+            float l = ulo[q * ncl + cb + p];
+            two_sum_acc(uh[r][q][p], l, __fmul_rn(h6, a));
+            ulo[q * ncl + cb + p] = l;
+            w = uh[r][q][p];
+          }
+          wout[q][p] = w;
+        }
       }
     }
 #pragma unroll
