@@ -69,7 +69,7 @@ FLOPS_PER_CELL_UPDATE = {"diffreact2d": (4 * (16 + 12) + 2 * 13) / 2.0,
 # captured kernels, scaled by the slices a launch runs (the kernel reads each
 # start state once; its results stay in L2).
 STENCIL_TRAFFIC = {"workload": "diffreact2d", "slices": 64,
-                   "bytes": {(8, 256, 2, 4): 16874496, (16, 128, 2, 4): 17022720}}
+                   "bytes": {(8, 256, 2, 4): 16828416, (16, 128, 2, 4): 17310976}}
 
 
 def traffic_per_launch(tf: dict, slices: float):
