@@ -340,7 +340,7 @@ rnp_status predict_core(rnp_ctx* c, const double* q, long long q_base, long long
       CK(launch_query32(c->A32, c->M, c->d, c->q32, c->B, fpart32, c->S32, c->cap, c->dP, pm,
                         npart32, gate, c->st));
     }
-    CK(launch_topm_ridge32(npart32, nn_chunks(c->d), c->Phi, c->cap, c->M, phi_dst + phi_base,
+    CK(launch_topm_ridge32(npart32, c->d, c->Phi, c->cap, c->M, phi_dst + phi_base,
                            phi_bstride, fpart32, features_chunks(c->d), c->zeta, c->dP, pm, c->B,
                            c->m, c->p.lambda, c->dist, c->alpha, c->idx, c->meff, c->flags + 0,
                            c->flags + 1, gate, c->st));
@@ -350,7 +350,7 @@ rnp_status predict_core(rnp_ctx* c, const double* q, long long q_base, long long
                            gate, c->st));
     CK(launch_query64(c->A, c->M, c->d, c->qbuf, c->B, c->feat_part, c->Sds, c->cap, c->dP, pm,
                       c->nn_part, gate, c->st));
-    CK(launch_topm_ridge(c->nn_part, nn_chunks(c->d), c->Phi, c->cap, c->M, phi_dst + phi_base,
+    CK(launch_topm_ridge(c->nn_part, c->d, c->Phi, c->cap, c->M, phi_dst + phi_base,
                          phi_bstride, c->feat_part, features_chunks(c->d), c->zeta, c->dP, pm,
                          c->B, c->m, c->p.lambda, c->dist, c->alpha, c->idx, c->meff,
                          c->flags + 0, c->flags + 1, gate, c->st));

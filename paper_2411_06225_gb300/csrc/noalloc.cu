@@ -139,7 +139,7 @@ extern "C" rnp_status rnp_randnet_predict_noalloc(const rnp_problem* prob, const
       (e = launch_features64(A, zeta, M, d, L.q, qrow, 1, L.phiq, Rows{nullptr, 0, M},
                              L.feat_part, nullptr, st)) ||
       (e = launch_nn_partial(L.q, S, P, d, L.P, P, 1, L.nn_part, nullptr, st)) ||
-      (e = launch_topm_ridge(L.nn_part, nn_chunks(d), Phi, P, M, L.phiq, M, nullptr, 0,
+      (e = launch_topm_ridge(L.nn_part, d, Phi, P, M, L.phiq, M, nullptr, 0,
                              nullptr, L.P, P, 1,
                              prob->m, prob->lambda, L.dist, L.alpha, L.idx, L.meff,
                              L.flags + 0, L.flags + 1, nullptr, st)) ||

@@ -315,7 +315,7 @@ cudaError_t launch_features32(const float* A, const double* zeta, int M, long lo
 // ---------------------------------------------------------------------------
 static const int kNnRows = 8;
 
-static long long nn_chunk_len(long long d) {
+__host__ __device__ inline long long nn_chunk_len(long long d) {
   long long ch = (d + 31) / 32;
   ch = ((ch + 255) / 256) * 256;
   return ch < 1024 ? 1024 : ch;
@@ -323,9 +323,56 @@ static long long nn_chunk_len(long long d) {
 
 int nn_chunks(long long d) { return (int)((d + nn_chunk_len(d) - 1) / nn_chunk_len(d)); }
 
+// Chunking of the distance sums for P stored rows: nn_chunks(d) chunks of
+// nn_chunk_len(d) while P x chunks stays within kNnTasks warp tasks; beyond,
+// fewer and longer chunks (about kNnTasks tasks, never more chunks than
+// nn_chunks(d)), so the selection kernel finishes fewer partials per row.
+// The partial and the selection kernels both derive it from (d, P).
+static constexpr int kNnTasks = 8192;
+__host__ __device__ inline void nn_split(long long d, int P, long long* chl, int* nch) {
+  const long long c0 = nn_chunk_len(d);
+  const int n0 = (int)((d + c0 - 1) / c0);
+  if ((long long)P * n0 <= kNnTasks) {
+    *chl = c0;
+    *nch = n0;
+    return;
+  }
+  const int want = P < kNnTasks ? kNnTasks / P : 1;
+  long long c = (d + want - 1) / want;
+  c = ((c + 255) / 256) * 256;
+  *chl = c;
+  *nch = (int)((d + c - 1) / c);
+}
+
+// sum over j in [j0, j1) of (q_j - S_j)^2 by one warp, fixed lane order
+template <typename T>
+__device__ __forceinline__ T warp_dist(const T* qb, const T* Sp, long long j0, long long j1,
+                                       int lane) {
+  T acc0 = T(0), acc1 = T(0);
+  long long j = j0 + lane;
+#pragma unroll 16
+  for (; j + 32 < j1; j += 64) {
+    const T t0 = qb[j] - Sp[j];
+    const T t1 = qb[j + 32] - Sp[j + 32];
+    acc0 = fma(t0, t0, acc0);
+    acc1 = fma(t1, t1, acc1);
+  }
+  if (j < j1) {
+    const T t0 = qb[j] - Sp[j];
+    acc0 = fma(t0, t0, acc0);
+  }
+  T acc = acc0 + acc1;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  return acc;
+}
+
 // Partial of member b, stored row p, chunk ch at part[(ch * B + b) * cap + p]
 // (chunk-major: the finishing threads, one per stored row, read consecutive
-// addresses).
+// addresses).  The grid (nch x gy blocks of kNnRows warps per member) does
+// not depend on P; with the default chunking block (ch, by) takes chunk ch
+// of rows by * kNnRows + warp (stride gy * kNnRows), otherwise the member's
+// warps stride over the (row, chunk) tasks of nn_split.
 template <typename T>
 __device__ __forceinline__ void nn_partial_body(const T* q, const T* S, long long cap,
                                                 long long d, long long chl, const int* P,
@@ -334,29 +381,28 @@ __device__ __forceinline__ void nn_partial_body(const T* q, const T* S, long lon
   if (gate && !gate[b]) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int Pb = P[b];
-  const long long j0 = (long long)ch * chl;
-  const long long j1 = (j0 + chl) < d ? j0 + chl : d;
   const T* qb = q + (long long)b * d;
-  // grid-stride over the stored rows: the grid does not depend on P
-  for (int p = by * kNnRows + warp; p < Pb; p += gy * kNnRows) {
-    const T* Sp = S + ((long long)b * cap + p) * d;
-    T acc0 = T(0), acc1 = T(0);
-    long long j = j0 + lane;
-#pragma unroll 16
-    for (; j + 32 < j1; j += 64) {
-      const T t0 = qb[j] - Sp[j];
-      const T t1 = qb[j + 32] - Sp[j + 32];
-      acc0 = fma(t0, t0, acc0);
-      acc1 = fma(t1, t1, acc1);
+  long long chl_e;
+  int nch_e;
+  nn_split(d, Pb, &chl_e, &nch_e);
+  if (nch_e == nch) {
+    const long long j0 = (long long)ch * chl;
+    const long long j1 = (j0 + chl) < d ? j0 + chl : d;
+    for (int p = by * kNnRows + warp; p < Pb; p += gy * kNnRows) {
+      const T acc = warp_dist<T>(qb, S + ((long long)b * cap + p) * d, j0, j1, lane);
+      if (lane == 0) part[((long long)ch * B + b) * cap + p] = acc;
     }
-    if (j < j1) {
-      const T t0 = qb[j] - Sp[j];
-      acc0 = fma(t0, t0, acc0);
+  } else {
+    const long long W = (long long)nch * gy * kNnRows;
+    const long long ntask = (long long)Pb * nch_e;
+    for (long long t = ((long long)by * nch + ch) * kNnRows + warp; t < ntask; t += W) {
+      const int p = (int)(t / nch_e);
+      const int c = (int)(t - (long long)p * nch_e);
+      const long long j0 = (long long)c * chl_e;
+      const long long j1 = (j0 + chl_e) < d ? j0 + chl_e : d;
+      const T acc = warp_dist<T>(qb, S + ((long long)b * cap + p) * d, j0, j1, lane);
+      if (lane == 0) part[((long long)c * B + b) * cap + p] = acc;
     }
-    T acc = acc0 + acc1;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) part[((long long)ch * B + b) * cap + p] = acc;
   }
 }
 
@@ -559,7 +605,7 @@ __device__ bool chol_general(const double* Kraw, const double* r, double lam, in
 // TP: type of the chunk partials (double in the FP64 path, float where the
 // query was computed in FP32; their sums are kept in TP).
 template <typename TP>
-__global__ void __launch_bounds__(256) k_topm_ridge(const TP* part, int nch,
+__global__ void __launch_bounds__(256) k_topm_ridge(const TP* part, long long d,
                                                     const double* Phi, long long cap, int M,
                                                     double* phiq, long long phiq_bstride,
                                                     const TP* fpart, int fnch,
@@ -571,6 +617,9 @@ __global__ void __launch_bounds__(256) k_topm_ridge(const TP* part, int nch,
   if (gate && !gate[b]) return;
   const int P = Pn[b];
   const int me = m < P ? m : P;
+  long long chl_unused;
+  int nch;                     // chunks of the distance partials (nn_split)
+  nn_split(d, P, &chl_unused, &nch);
   constexpr int kWarps = 8;  // blockDim.x == 256
   __shared__ int sel[RNP_MAX_M];
   __shared__ unsigned long long ck[kWarps * RNP_MAX_M];
@@ -817,38 +866,38 @@ __global__ void __launch_bounds__(256) k_topm_ridge(const TP* part, int nch,
 }
 
 template <typename TP>
-static cudaError_t launch_topm_t(const TP* part, int nch, const double* Phi, long long cap,
+static cudaError_t launch_topm_t(const TP* part, long long d, const double* Phi, long long cap,
                                  int M, double* phiq, long long phiq_bstride, const TP* fpart,
                                  int fnch, const double* zeta, const int* P, int B, int m,
                                  double lambda, double* dist, double* alpha, int* idx,
                                  int* meff, int* esc_count, int* fail, const int* gate,
                                  cudaStream_t st) {
   count_launches(1);
-  k_topm_ridge<TP><<<B, 256, 0, st>>>(part, nch, Phi, cap, M, phiq, phiq_bstride, fpart, fnch,
+  k_topm_ridge<TP><<<B, 256, 0, st>>>(part, d, Phi, cap, M, phiq, phiq_bstride, fpart, fnch,
                                       zeta, P, m, lambda, dist, alpha, idx, meff, esc_count,
                                       fail, gate);
   return cudaGetLastError();
 }
 
-cudaError_t launch_topm_ridge(const double* part, int nch, const double* Phi, long long cap,
+cudaError_t launch_topm_ridge(const double* part, long long d, const double* Phi, long long cap,
                               int M, double* phiq, long long phiq_bstride, const double* fpart,
                               int fnch, const double* zeta, const int* P, int Pmax, int B,
                               int m, double lambda, double* dist, double* alpha, int* idx,
                               int* meff, int* esc_count, int* fail, const int* gate,
                               cudaStream_t st) {
   (void)Pmax;
-  return launch_topm_t<double>(part, nch, Phi, cap, M, phiq, phiq_bstride, fpart, fnch, zeta, P,
+  return launch_topm_t<double>(part, d, Phi, cap, M, phiq, phiq_bstride, fpart, fnch, zeta, P,
                                B, m, lambda, dist, alpha, idx, meff, esc_count, fail, gate, st);
 }
 
-cudaError_t launch_topm_ridge32(const float* part, int nch, const double* Phi, long long cap,
+cudaError_t launch_topm_ridge32(const float* part, long long d, const double* Phi, long long cap,
                                 int M, double* phiq, long long phiq_bstride, const float* fpart,
                                 int fnch, const double* zeta, const int* P, int Pmax, int B,
                                 int m, double lambda, double* dist, double* alpha, int* idx,
                                 int* meff, int* esc_count, int* fail, const int* gate,
                                 cudaStream_t st) {
   (void)Pmax;
-  return launch_topm_t<float>(part, nch, Phi, cap, M, phiq, phiq_bstride, fpart, fnch, zeta, P,
+  return launch_topm_t<float>(part, d, Phi, cap, M, phiq, phiq_bstride, fpart, fnch, zeta, P,
                               B, m, lambda, dist, alpha, idx, meff, esc_count, fail, gate, st);
 }
 

@@ -187,11 +187,13 @@ cudaError_t launch_query32(const float* A, int M, long long d, const float* q, i
                            int Pmax, float* npart, const int* gate, cudaStream_t st);
 
 // Per member: (if fpart != null) finish the query features phi_q from their
-// chunk partials into phiq[b]; finish distances, select the m nearest (ties
+// chunk partials into phiq[b]; finish distances (d: the state dimension; the
+// partials are chunked as the partial kernels chunk a member with P stored
+// rows), select the m nearest (ties
 // -> lower index), build the dual ridge system from the stored features and
 // phi_q, solve by Cholesky (lambda x10 on a non-positive pivot, at most 4
 // times) and write alpha[b*RNP_MAX_M + l], idx[b*RNP_MAX_M + l], meff[b].
-cudaError_t launch_topm_ridge(const double* part, int nch, const double* Phi,
+cudaError_t launch_topm_ridge(const double* part, long long d, const double* Phi,
                               long long cap, int M, double* phiq,
                               long long phiq_bstride, const double* fpart, int fnch,
                               const double* zeta, const int* P, int Pmax,
@@ -200,7 +202,7 @@ cudaError_t launch_topm_ridge(const double* part, int nch, const double* Phi,
                               int* esc_count, int* fail, const int* gate,
                               cudaStream_t st);
 // The same with FP32 chunk partials (from launch_query32 / launch_nn_partial32).
-cudaError_t launch_topm_ridge32(const float* part, int nch, const double* Phi,
+cudaError_t launch_topm_ridge32(const float* part, long long d, const double* Phi,
                                 long long cap, int M, double* phiq,
                                 long long phiq_bstride, const float* fpart, int fnch,
                                 const double* zeta, const int* P, int Pmax,

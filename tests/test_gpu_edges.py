@@ -101,16 +101,21 @@ def test_odd_grid_solve(R, orc, precision):
     assert rel(U, Uo) <= (1e-10 if precision == "fp64" else 1e-5)
 
 
-@pytest.mark.parametrize("P,m", [(300, 4), (1100, 4), (2600, 3), (2600, 8), (2600, 9)])
-def test_predict_large_dataset_ties_match_oracle(R, orc, P, m):
+@pytest.mark.parametrize("P,m,nx", [(300, 4, 8), (1100, 4, 8), (2600, 3, 8), (2600, 8, 8),
+                                    (2600, 9, 8),
+                                    # 8 chunks per row by default: beyond 1024 rows
+                                    # the distance sums use fewer, longer chunks
+                                    (1500, 4, 64), (3000, 3, 64)])
+def test_predict_large_dataset_ties_match_oracle(R, orc, P, m, nx):
     """The m-nearest selection over more stored rows than the selecting CTA
-    has threads (up to ten rows per thread), with the register lists (m <= 8)
-    and past them (m = 9).  Five exact copies of the query's nearest input,
+    has threads (up to twelve rows per thread), with the register lists
+    (m <= 8) and past them (m = 9), and with the distance sums in their
+    default and in their long-chunk split.  Five exact copies of the query's nearest input,
     spread over the dataset, tie at the m-th place: the lower indices win
     (App. B's order statistics, ties by index, as in the oracle), and the
     copies carry different targets, so a wrong pick changes the
     prediction."""
-    cfg = W.config("diffreact2d", nx=8, ny=8, M=40, m=m)
+    cfg = W.config("diffreact2d", nx=nx, ny=nx, M=40, m=m)
     p = orc.problem(cfg)
     d = W.dim(cfg)
     rng = np.random.default_rng(P + m)
