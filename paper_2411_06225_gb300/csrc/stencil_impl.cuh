@@ -763,8 +763,11 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
   const float dt = P.fdt, h2 = P.fh2, h6 = P.fh6;
   constexpr int NC = KT<KP>::NC, DIMS = KT<KP>::DIMS;
   const int ncl = P.mcl;  // component stride of the low words (no ghost rows)
-  // diffusion-reaction with two x-points per thread: packed FP32
-  constexpr bool kPacked = PX == 2 && KP == KP_DIFFREACT;
+  // two-species reaction-diffusion with an even number of x-points per
+  // thread: packed FP32 on pairs of points; kk[kLx..] = 1/hx^2, 1/hy^2, 1/hz^2
+  constexpr bool kPacked =
+      PX % 2 == 0 && (KP == KP_DIFFREACT || KP == KP_BRUSS2 || KP == KP_BRUSS3);
+  constexpr int kLx = KP == KP_DIFFREACT ? 3 : 5;
   // Only the shallow-water fluxes tell the two outer neighbours apart; the
   // other right-hand sides take their sum.
   constexpr bool kOrdered = KP == KP_SWE;
@@ -832,50 +835,74 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
     }
     float wout[NC][PX];
     if constexpr (kPacked) {
-      // both x-points of the tile in packed FP32: the outer neighbours pair
-      // up as loaded; in x, point 0's east neighbour is point 1 and point
-      // 1's west neighbour point 0, the other two the adjacent tiles' edges
-      float2 kq[NC], Cq[NC], lq[NC];
+      // pairs of x-points (2i, 2i + 1) in packed FP32: the outer neighbours
+      // pair up as loaded; in x, point 2i's east neighbour is point 2i + 1
+      // and point 2i + 1's west neighbour point 2i, the other two are the
+      // tile's or the adjacent tiles' values
 #pragma unroll
-      for (int q = 0; q < NC; ++q) {
-        const float2 C = pk(cur[q][0], cur[q][1]);
-        // E + W of both points, as two scalar adds that write the pair
-        const float2 EW = pk(cur[q][1] + ew[q], cur[q][0] + ee[q]);
-        const float2 NS = add2(pk(ahead[q][0], ahead[q][1]), pk(back[q][0], back[q][1]));
-        const float2 lx = mul2(fma2(pk1(-2.f), C, EW), pk1(kk[3]));
-        lq[q] = fma2(fma2(pk1(-2.f), C, NS), pk1(kk[4]), lx);
-        Cq[q] = C;
-      }
-      // Du lap u + (u - u^3 - c - v);  Dv lap v + (u - v)
-      const float2 a = Cq[0], b = Cq[1];
-      const float2 a3 = mul2(mul2(a, a), a);
-      kq[0] = fma2(pk1(kk[0]), lq[0], sub2(sub2(sub2(a, a3), pk1(kk[2])), b));
-      kq[1] = fma2(pk1(kk[1]), lq[1], sub2(a, b));
+      for (int pp = 0; pp < PX / 2; ++pp) {
+        const int p0 = 2 * pp, p1 = 2 * pp + 1;
+        float2 kq[NC], Cq[NC], lq[NC];
 #pragma unroll
-      for (int q = 0; q < NC; ++q) {
-        float2 U = pk(uh[r][q][0], uh[r][q][1]);
-        float2 w;
-        if (euler) {
-          float2 l = *reinterpret_cast<const float2*>(ulo + q * ncl + cb);
-          two_sum_acc2(U, l, mul2(pk1(dt), kq[q]));
-          *reinterpret_cast<float2*>(ulo + q * ncl + cb) = l;
-          w = U;
-        } else if (STAGE == 0) {
-          acc[r][q][0] = kq[q].x; acc[r][q][1] = kq[q].y;
-          w = fma2(pk1(h2), kq[q], U);
-        } else if (STAGE == 1 || STAGE == 2) {
-          const float2 A2 = fma2(pk1(2.f), kq[q], pk(acc[r][q][0], acc[r][q][1]));
-          acc[r][q][0] = A2.x; acc[r][q][1] = A2.y;
-          w = fma2(pk1(STAGE == 1 ? h2 : dt), kq[q], U);
-        } else {
-          const float2 A2 = add2(pk(acc[r][q][0], acc[r][q][1]), kq[q]);
-          float2 l = *reinterpret_cast<const float2*>(ulo + q * ncl + cb);
-          two_sum_acc2(U, l, mul2(pk1(h6), A2));
-          *reinterpret_cast<float2*>(ulo + q * ncl + cb) = l;
-          w = U;
+        for (int q = 0; q < NC; ++q) {
+          const float w0 = p0 > 0 ? cur[q][p0 - 1] : ew[q];
+          const float e1 = p1 + 1 < PX ? cur[q][p1 + 1] : ee[q];
+          const float2 C = pk(cur[q][p0], cur[q][p1]);
+          // E + W of both points, as two scalar adds that write the pair
+          const float2 EW = pk(cur[q][p1] + w0, e1 + cur[q][p0]);
+          const float2 hi = pk(ahead[q][p0], ahead[q][p1]);
+          const float2 lo = pk(back[q][p0], back[q][p1]);
+          float2 l;
+          if constexpr (DIMS == 2) {
+            const float2 lx = mul2(fma2(pk1(-2.f), C, EW), pk1(kk[kLx]));
+            l = fma2(fma2(pk1(-2.f), C, add2(hi, lo)), pk1(kk[kLx + 1]), lx);
+          } else {
+            const float2 NS = add2(pk(yn[q][p0], yn[q][p1]), pk(ys[q][p0], ys[q][p1]));
+            const float2 lx = mul2(fma2(pk1(-2.f), C, EW), pk1(kk[kLx]));
+            const float2 ly = fma2(fma2(pk1(-2.f), C, NS), pk1(kk[kLx + 1]), lx);
+            l = fma2(fma2(pk1(-2.f), C, add2(hi, lo)), pk1(kk[kLx + 2]), ly);
+          }
+          lq[q] = l;
+          Cq[q] = C;
         }
-        uh[r][q][0] = U.x; uh[r][q][1] = U.y;
-        wout[q][0] = w.x; wout[q][1] = w.y;
+        const float2 a = Cq[0], b = Cq[1];
+        if constexpr (KP == KP_DIFFREACT) {
+          // Du lap u + (u - u^3 - c - v);  Dv lap v + (u - v)
+          const float2 a3 = mul2(mul2(a, a), a);
+          kq[0] = fma2(pk1(kk[0]), lq[0], sub2(sub2(sub2(a, a3), pk1(kk[2])), b));
+          kq[1] = fma2(pk1(kk[1]), lq[1], sub2(a, b));
+        } else {
+          // D0 lap u + (a - (1 + b) u + v u^2);  D1 lap v + (b u - v u^2)
+          const float2 ba2 = mul2(b, mul2(a, a));
+          kq[0] = fma2(pk1(kk[2]), lq[0], add2(fma2(pk1(-kk[4]), a, pk1(kk[0])), ba2));
+          kq[1] = fma2(pk1(kk[3]), lq[1], fma2(pk1(kk[1]), a, mul2(pk1(-1.f), ba2)));
+        }
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+          float2 U = pk(uh[r][q][p0], uh[r][q][p1]);
+          float2 w;
+          if (euler) {
+            float2 l = *reinterpret_cast<const float2*>(ulo + q * ncl + cb + p0);
+            two_sum_acc2(U, l, mul2(pk1(dt), kq[q]));
+            *reinterpret_cast<float2*>(ulo + q * ncl + cb + p0) = l;
+            w = U;
+          } else if (STAGE == 0) {
+            acc[r][q][p0] = kq[q].x; acc[r][q][p1] = kq[q].y;
+            w = fma2(pk1(h2), kq[q], U);
+          } else if (STAGE == 1 || STAGE == 2) {
+            const float2 A2 = fma2(pk1(2.f), kq[q], pk(acc[r][q][p0], acc[r][q][p1]));
+            acc[r][q][p0] = A2.x; acc[r][q][p1] = A2.y;
+            w = fma2(pk1(STAGE == 1 ? h2 : dt), kq[q], U);
+          } else {
+            const float2 A2 = add2(pk(acc[r][q][p0], acc[r][q][p1]), kq[q]);
+            float2 l = *reinterpret_cast<const float2*>(ulo + q * ncl + cb + p0);
+            two_sum_acc2(U, l, mul2(pk1(h6), A2));
+            *reinterpret_cast<float2*>(ulo + q * ncl + cb + p0) = l;
+            w = U;
+          }
+          uh[r][q][p0] = U.x; uh[r][q][p1] = U.y;
+          wout[q][p0] = w.x; wout[q][p1] = w.y;
+        }
       }
     } else {
 #pragma unroll
