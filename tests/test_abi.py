@@ -66,3 +66,39 @@ def test_create_rejects_bad_problem_without_touching_a_gpu(built):
     p = rnp.problem(W.config("burgers1d"), m=64)
     assert built.rnp_create(C.byref(p), None, C.byref(ctx)) == rnp.RNP_EINVAL
     assert rnp.dim(rnp.problem(W.config("bruss3d"))) == 2 * 40**3
+
+
+def test_create_refuses_unsupported_solver_options_without_a_gpu(built):
+    import numpy as np
+    import workloads as W
+    ctx = C.c_void_p()
+    # the eighth-order fine solver runs in FP64 only
+    p = rnp.problem(W.config("burgers1d", fscheme="rk8"), precision="mixed")
+    assert built.rnp_create(C.byref(p), None, C.byref(ctx)) == rnp.RNP_EINVAL
+    assert b"RK8" in built.rnp_last_error(None)
+    # an unknown fine integrator
+    p = rnp.problem(W.config("burgers1d"))
+    p.fscheme = 7
+    assert built.rnp_create(C.byref(p), None, C.byref(ctx)) == rnp.RNP_EINVAL
+    assert b"fscheme" in built.rnp_last_error(None)
+    # a bottom profile belongs to shallow water only
+    cfg = W.config("diffreact2d", nx=8, ny=8)
+    cfg["bathymetry"] = np.zeros((8, 8))
+    p = rnp.problem(cfg)
+    assert built.rnp_create(C.byref(p), None, C.byref(ctx)) == rnp.RNP_EINVAL
+    assert b"bathymetry" in built.rnp_last_error(None)
+    with pytest.raises(ValueError):
+        rnp.problem(dict(W.config("swe_box"), bathymetry=np.zeros(7)))
+
+
+def test_serving_pools_separate_bottoms_and_solvers():
+    import numpy as np
+    import workloads as W
+    from paper_2411_06225_gb300.serve import class_key
+    base = W.config("swe_box", nx=20, ny=10)
+    b1 = dict(base, bathymetry=np.zeros((10, 20)))
+    b2 = dict(base, bathymetry=np.full((10, 20), 0.1))
+    assert class_key(b1) == class_key(dict(base, bathymetry=np.zeros((10, 20))))
+    assert class_key(b1) != class_key(b2) != class_key(base)
+    assert class_key(base) != class_key(dict(base, bc="periodic"))
+    assert class_key(base) != class_key(dict(base, fscheme="rk8"))
