@@ -179,14 +179,14 @@ def aggregate(t_local: float, work_local: float, dist=None, device=None):
 
 def cpu_baseline(seconds_hint: float = 20.0) -> dict:
     """The FP64 oracle on the host cores: a bounded sample of the same
-    workload (same grid, slices and coarse solver; nF cut to 150 of 2000
+    workload (same grid, slices and coarse solver; nF cut to 1000 of 2000
     fine steps per slice: about 12 s on 16 cores), reported in fine
     cell-updates per second."""
     import oracle
     cores = os.cpu_count() or 1
     oracle.set_threads(cores)
     full = W.config(WORKLOAD)
-    cfg = W.config(WORKLOAD, nF=min(150, full["nF"]))
+    cfg = W.config(WORKLOAD, nF=min(1000, full["nF"]))
     p = oracle.problem(cfg)
     u0 = W.initial_condition(cfg)[0]
     t0 = time.perf_counter()
@@ -217,8 +217,8 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD} (CPU sample, nF=150)", "grid": "128x128x2",
-                   "N": 64, "nF": 150, "nG": 8},
+        "config": {"workload": f"{WORKLOAD} (CPU sample, nF=1000)", "grid": "128x128x2",
+                   "N": 64, "nF": 1000, "nG": 8},
         "cpu_baseline": {"kind": "oracle", "cores": base["cores"], "sample": base["sample"],
                          "value": value, "unit": UNIT},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
