@@ -392,7 +392,16 @@ def run_gpu(args):
                          "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
                          "frac": achieved / peak_alu, "traffic": traffic,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock "
-                                        f"{pk.get('sm_max_mhz', 2070.0)} MHz (MEASURED_PEAKS)"},
+                                        f"{pk.get('sm_max_mhz', 2070.0)} MHz (MEASURED_PEAKS)",
+                         # the same kernel against HBM: its measured DRAM bytes
+                         # per launch over the launch time, of the measured copy
+                         # bandwidth (the state lives in shared memory, so this
+                         # stays far below 1)
+                         "hbm": None if traffic is None else {
+                             "achieved_gbs": traffic / (statistics.mean(fine_ms) / 1e3) / 1e9,
+                             "peak_gbs": pk["hbm_gbs"],
+                             "frac": traffic / (statistics.mean(fine_ms) / 1e3) / 1e9
+                             / pk["hbm_gbs"]}},
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(u0_h.numel() * 8),
                     "d2h_bytes_per_step": int(U_h.numel() * 8),

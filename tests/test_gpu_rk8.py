@@ -131,3 +131,19 @@ def test_rk8_refusals(R):
     # the plain execution has no such limit
     with R.Solver(R.problem(big, precision="fp64", exec="plain")) as s:
         assert s is not None
+
+
+def test_rk8_robustness_burgers_full_size_sampled(R, orc):
+    """The robustness study's Burgers with the paper's RK8 (d = 128,
+    N = 128 on [0, 5.9], 313 steps per slice): F on all 128 slices in one
+    fused launch, sampled slices bit-identical to the oracle."""
+    from paper_2411_06225_gb300.robustness import system_config
+    cfg = system_config("burgers", fine="rk8")
+    p = orc.problem(cfg)
+    u0 = W.initial_condition(cfg)
+    with R.Solver(R.problem(cfg, precision="fp64")) as s:
+        U0 = host(s.coarse_sweep(0, dev(u0)))
+        starts = U0[:, :cfg["N"]].copy()
+        Fv = host(s.fine_batch(dev(starts)))
+    for j in (0, 64, 127):
+        assert np.array_equal(Fv[0, j], orc.fine(p, starts[0, j])), j

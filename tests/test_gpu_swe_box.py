@@ -154,3 +154,26 @@ def test_bathymetry_refused_for_other_pdes(R):
     with pytest.raises(R.RnpError) as e:
         R.Solver(R.problem(cfg))
     assert e.value.status == R.RNP_EINVAL
+
+
+def test_full_size_box_sampled(R, orc):
+    """The paper's dam-break workload at full size, in the bench's launch
+    configuration (F on all 235 slice starts in one launch, autotuned
+    tiling): sampled slices within the FP32 bound of the FP64 oracle, and
+    a full mixed solve whose states satisfy |U_i - F(U_{i-1})| <= 10 tol
+    on sampled slices."""
+    cfg = W.config("swe_box")
+    p = orc.problem(cfg)
+    u0 = W.initial_condition(cfg)
+    with R.Solver(R.problem(cfg, precision="mixed", autotune=1)) as s:
+        U0 = host(s.coarse_sweep(0, dev(u0)))
+        starts = U0[:, :cfg["N"]].copy()
+        Fv = host(s.fine_batch(dev(starts)))
+        for j in (0, 117, 234):
+            assert rel(Fv[0, j], orc.fine(p, starts[0, j])) <= 2e-7, j
+        s.reset()
+        U, st = s.solve(dev(u0))
+        U = host(U)[0]
+    assert st["converged"]
+    for i in (3, 120, 235):
+        assert np.abs(U[i] - orc.fine(p, U[i - 1])).max() <= 10 * cfg["tol"], i
