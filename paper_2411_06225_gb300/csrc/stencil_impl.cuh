@@ -567,6 +567,9 @@ __global__ void k_stage_plain(const PlainParams P) {
 //    RS consecutive outer rows: the outer-axis neighbours come from a rolling
 //    window of registers, only the x neighbours (and y in 3D) are loaded;
 //  * the four Runge-Kutta stages are unrolled at compile time;
+//  * for the two-species reaction-diffusion operators (diffusion-reaction,
+//    Brusselator) pairs of x-points share packed FP32 instructions
+//    (fadd2 / fmul2 / ffma2), halving the arithmetic instructions;
 //  * no CTA reads another CTA's stage buffer.  The threads that own a CTA's
 //    first or last outer row push that row's new stage values into the
 //    neighbouring CTA's halo rows (st.async into distributed shared memory,
