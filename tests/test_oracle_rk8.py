@@ -148,3 +148,25 @@ def test_exact_at_zero_tolerance_rk8(orc):
     rc, U, st, _ = orc.solve(p, u0)
     assert st.K == cfg["N"]
     assert np.array_equal(U, orc.serial_fine(p, u0))
+
+
+@pytest.mark.parametrize("k", [1, 4, 9])
+def test_rk8_noflux_cosine_mode(orc, k):
+    """With no-flux walls (cell-centred grid) cos(pi k x / L) is an
+    eigenvector of the heat operator with eigenvalue
+    -(4 D / h^2) sin^2(pi k h / 2L); one RK8 step multiplies it by the
+    tableau's stability function."""
+    n, D, L = 24, 0.05, 1.0
+    cfg = _heat1d(n, D, L)
+    cfg["bc"] = "neumann"
+    p = orc.problem(cfg)
+    h = L / n
+    x = (np.arange(n) + 0.5) * h
+    u0 = np.cos(math.pi * k * x / L)
+    lam = -(4.0 * D / h**2) * math.sin(math.pi * k * h / (2.0 * L)) ** 2
+    dt = 2.5 / (4.0 * D / h**2)
+    A, b, _ = orc.rk8_tableau()
+    z = dt * lam
+    R = 1.0 + z * (b @ np.linalg.solve(np.eye(11) - z * A, np.ones(11)))
+    got = orc.rk8(p, u0, dt, 30)
+    assert np.abs(got - u0 * R**30).max() <= 1e-13
