@@ -253,3 +253,47 @@ def test_nonfinite_state_is_reported(R):
         with pytest.raises(R.RnpError) as e:
             s.solve(dev(u0))
         assert e.value.status == R.RNP_ENONFINITE
+
+
+@pytest.mark.parametrize("name,kw", [
+    ("diffreact2d", dict(nx=16, ny=16, N=8, nF=40, M=32, m=3, tN=0.5)),
+    ("burgers1d", dict(nx=64, N=10, nF=200, nG=16, M=40, m=4)),
+])
+def test_stepwise_replay_of_one_sweep(R, orc, name, kw):
+    """One sweep of Eq. 3 in isolation: the oracle's k = 0 trajectory, the
+    pairs (U_i, F(U_i) - G(U_i)) that iteration 1 appends and the scaling of
+    Alg. 1 are given to the GPU context, which runs the sweep
+    U_i = G(U_{i-1}) + f_hat(U_{i-1}) from the exact leftmost slice.  Each
+    state matches the oracle replaying the same step (its G and its
+    prediction from the same dataset) within 1e-10, so a near-tie flip of
+    the m-nearest selection or a drift of the correction shows at its step
+    rather than as a changed K."""
+    cfg = W.config(name, **kw)
+    p = orc.problem(cfg)
+    N, nc = cfg["N"], W.ncomp(cfg)
+    u0 = W.initial_condition(cfg)[0]
+    U0 = [u0]
+    for _ in range(N):
+        U0.append(orc.coarse(p, U0[-1]))
+    U0 = np.stack(U0)
+    c, r = orc.scaling(p, U0)
+    c[nc:], r[nc:] = 0.0, 1.0
+    A, z = orc.weights(p)
+    starts = U0[:N]
+    Y = np.stack([orc.fine(p, s) - orc.coarse(p, s) for s in starts])
+    S = np.stack([orc.scale(p, c, r, s) for s in starts])
+    Phi = np.stack([orc.features(A, z, sr) for sr in S])
+    ref = [u0, orc.fine(p, u0)]
+    for _ in range(2, N + 1):
+        prev = ref[-1]
+        rc, corr, _ = orc.predict(p, S, Y, Phi, A, z, c, r, prev)
+        assert rc >= 0
+        ref.append(orc.coarse(p, prev) + corr)
+    ref = np.stack(ref)
+    with R.Solver(R.problem(cfg, precision="fp64", max_pairs=N)) as s:
+        s.set_scaling(c[None], r[None])
+        s.randnet_fit(dev(starts[None]), dev(Y[None]))
+        U = host(s.coarse_sweep(1, dev(ref[1][None])))[0]
+    for i in range(1, N + 1):
+        e = np.abs(U[i] - ref[i]).max() / np.abs(ref[i]).max()
+        assert e <= 1e-10, (i, e)
