@@ -24,6 +24,12 @@
  *
  * Every floating-point expression is evaluated in the order written in
  * the source, compiled with -ffp-contract=off (no fused multiply-add).
+ *
+ * Pins (tests/test_oracle_*.py): every function is checked against closed
+ * forms, invariants, brute force, library routines or published vectors.
+ * orc_solve's iterates for tol > 0 have no value printed in the paper:
+ * beyond K <= N, eps = 0 (K = N, bitwise the serial fine solution), G = F
+ * (K = 1) and the converged error near tol, they are "parity unpinned".
  */
 #ifndef RNP_ORACLE_H
 #define RNP_ORACLE_H
