@@ -7,16 +7,18 @@
  * The library solves the initial value problem of Eq. 1,
  *     du/dt = h(u),  t in [t0, tN],  u(t0) = u0,  u in R^d,
  * split into N time slices (Sec. 2), with a cheap coarse propagator G
- * (forward Euler or RK4), an accurate fine propagator F (classic RK4) and
- * the RandNet correction of Eq. randnet: a fixed random hidden layer
+ * (forward Euler or RK4), an accurate fine propagator F (classic RK4, or
+ * the eighth-order RK8 the paper uses in Sec. 5.1-5.2) and the RandNet
+ * correction of Eq. randnet: a fixed random hidden layer
  * (Eq. HA, weights and biases U(-1,1), ReLU) whose linear readout is a
  * ridge fit (Eq. ridgeless) on the m nearest stored pairs (App. B), inside
  * the predictor-corrector sweep of Eq. 3 and the loop of Alg. 1.
  *
  * Conventions shared by every call
  *   - Array arguments are caller-owned DEVICE pointers to contiguous FP64
- *     data on the device that was current at rnp_create.  The library never
- *     frees them and never keeps them past the call.
+ *     data on the device that was current at rnp_create, except where a
+ *     call or field says "host".  The library never frees them and never
+ *     keeps them past the call.
  *   - d = ncomp * nx * ny * nz unknowns per state, component-major, then z,
  *     then y, then x (x fastest).  ncomp: Burgers/heat/advection 1,
  *     diffusion-reaction and Brusselator 2 (u then v), shallow water 3
