@@ -54,3 +54,34 @@ def test_reference_other_ranks_print_nothing(bench_mod, capsys, monkeypatch):
     assert bench.run_reference(_args(2, 1, gpus=2)) == 0
     assert capsys.readouterr().out.strip() == ""
     assert calls == []
+
+
+def test_dam_break_workload_recipe():
+    """The paper's dam break as DESIGN states it: 10 x 5 box, 100 x 50
+    cells, walls, N = 235 on [0, 20], G = Euler x 7, F steps by the CFL
+    rule, m = 3; depth 1 plus the bivariate normal density of the column
+    (mean (2.5, 1.5) in box coordinates, covariance 0.25 I), no momentum."""
+    import math
+
+    import numpy as np
+
+    import bench
+    import workloads as W
+    cfg = W.config("swe_box")
+    assert (cfg["nx"], cfg["ny"], cfg["lx"], cfg["ly"]) == (100, 50, 10.0, 5.0)
+    assert (cfg["N"], cfg["tN"], cfg["nG"], cfg["m"], cfg["bc"]) == (235, 20.0, 7, 3, "neumann")
+    assert cfg["nF"] == W.swe_steps(cfg)[0] == 35
+    u0 = W.initial_condition(cfg)[0]
+    n = 100 * 50
+    h = u0[:n].reshape(50, 100)
+    assert np.all(u0[n:] == 0.0)
+    j, i = np.unravel_index(np.argmax(h), h.shape)
+    assert abs((i + 0.5) * 0.1 - 2.5) <= 0.05 and abs((j + 0.5) * 0.1 - 1.5) <= 0.05
+    assert h.max() <= 1.0 + 1.0 / (2 * math.pi * 0.25) + 1e-12
+    assert h.min() >= 1.0
+    # the column's volume above depth 1 is the density's mass inside the
+    # box: the bottom wall is 3 sigma below the centre, the others farther
+    phi = lambda z: 0.5 * math.erfc(-z / math.sqrt(2.0))
+    inside = (phi(15.0) - phi(-5.0)) * (phi(7.0) - phi(-3.0))
+    assert abs((h - 1.0).sum() * 0.1 * 0.1 - inside) < 1e-5
+    assert "walls" in bench.describe(cfg) and "F=RK4x35" in bench.describe(cfg)
