@@ -83,5 +83,5 @@ def test_dam_break_workload_recipe():
     # box: the bottom wall is 3 sigma below the centre, the others farther
     phi = lambda z: 0.5 * math.erfc(-z / math.sqrt(2.0))
     inside = (phi(15.0) - phi(-5.0)) * (phi(7.0) - phi(-3.0))
-    assert abs((h - 1.0).sum() * 0.1 * 0.1 - inside) < 1e-5
+    assert abs((h - 1.0).sum() * 0.1 * 0.1 - inside) < 1e-4   # midpoint rule, h = 0.1
     assert "walls" in bench.describe(cfg) and "F=RK4x35" in bench.describe(cfg)
