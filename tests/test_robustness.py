@@ -32,6 +32,17 @@ def test_system_sizes():
     assert W.dim(R.system_config("diffreact")) == 722
 
 
+def test_paper_burgers_setting_and_fine_solvers():
+    # the paper's Burgers experiment: N = 128 on [0, 5.9], G = Euler x 4;
+    # with RK8 the paper's 4e4 fine steps spread over the 128 slices
+    b4, b8 = R.system_config("burgers"), R.system_config("burgers", "rk8")
+    assert (b4["N"], b4["tN"], b4["nG"], b4["ic"]) == (128, 5.9, 4, "cos9")
+    assert (b4["fscheme"], b4["nF"]) == ("rk4", 100)
+    assert (b8["fscheme"], b8["nF"]) == ("rk8", 313) and 313 * 128 >= 40000
+    with pytest.raises(ValueError):
+        R.system_config("burgers", "rk5")
+
+
 @pytest.mark.gpu
 @pytest.mark.parametrize("system", ["burgers", "diffreact"])
 def test_small_grid_matches_the_oracle(orc, system):
