@@ -204,6 +204,8 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
+    full = W.config(WORKLOAD)
+    cfg = W.config(WORKLOAD, nF=min(1000, full["nF"]))   # the cpu_baseline sample
     samples = []
     base = None
     for i in range(args.warmup + args.steps):
@@ -217,8 +219,9 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD} (CPU sample, nF=1000)", "grid": "128x128x2",
-                   "N": 64, "nF": 1000, "nG": 8},
+        "config": {"workload": f"{describe(cfg)} (CPU sample: nF={cfg['nF']} of {full['nF']})",
+                   "grid": "x".join(str(v) for v in (cfg["nx"], cfg["ny"], cfg["nz"]) if v > 1)
+                   + f"x{W.ncomp(cfg)}", "N": cfg["N"], "nF": cfg["nF"], "nG": cfg["nG"]},
         "cpu_baseline": {"kind": "oracle", "cores": base["cores"], "sample": base["sample"],
                          "value": value, "unit": UNIT},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,

@@ -44,6 +44,18 @@ def test_reference_line(bench_mod, capsys, monkeypatch):
     assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT,
                            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert line["higher_is_better"] is True and line["vs_baseline"] is None
+    assert line["config"]["grid"] == "128x128x2" and line["config"]["N"] == 64
+    assert line["config"]["nF"] == 1000 and "diffreact2d" in line["config"]["workload"]
+
+
+def test_reference_line_names_its_workload(bench_mod, capsys, monkeypatch):
+    bench, calls = bench_mod
+    monkeypatch.delenv("RANK", raising=False)
+    monkeypatch.setattr(bench, "WORKLOAD", "swe_box")
+    assert bench.run_reference(_args(1, 0)) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["config"]["grid"] == "100x50x3" and line["config"]["N"] == 235
+    assert line["config"]["nF"] == 35 and "walls" in line["config"]["workload"]
 
 
 def test_reference_other_ranks_print_nothing(bench_mod, capsys, monkeypatch):
