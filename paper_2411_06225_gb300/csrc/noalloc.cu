@@ -10,8 +10,6 @@
 // and the intermediate values (scaled query, features, distance partials,
 // ridge coefficients) live in one file-scope device array below, of fixed
 // size, that every GPU loading this library keeps until the process exits.
-#include <mutex>
-
 #include "rnp_internal.h"
 
 namespace rnp {
@@ -71,24 +69,16 @@ __global__ void k_na_epilogue(const int* flags, int* status) {
   *status = flags[1] ? RNP_ENONFINITE : (flags[2] ? RNP_ENONFINITE : RNP_OK);
 }
 
-// Device address of the scratch array, looked up once per device with that
-// device current (a host-side mention of g_na_scratch is only a stand-in).
-static std::mutex g_na_mu;
-static double* g_na_addr[64] = {nullptr};
-
+// Device address of the scratch array on the current device (a host-side
+// mention of g_na_scratch is only a stand-in).  Looked up on every call: the
+// first lookup on a device loads the module there, later ones are a table
+// read, and a lookup per call stays right if the device's context is reset
+// and the module reloads elsewhere.
 static cudaError_t scratch_for_current_device(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lk(g_na_mu);
-  if (!g_na_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_na_scratch);
-    if (e != cudaSuccess) return e;
-    g_na_addr[dev] = static_cast<double*>(p);
-  }
-  *out = g_na_addr[dev];
+  *out = static_cast<double*>(p);
   return cudaSuccess;
 }
 
