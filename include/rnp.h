@@ -138,7 +138,7 @@ typedef struct {
   int exec;               /* rnp_exec                                       */
   int batch;              /* independent initial conditions, 1..64          */
   int cluster;            /* fused stencil: CTAs per slice (0 = auto)       */
-  int threads;            /* fused stencil: threads per CTA (0 = auto)      */
+  int threads;            /* fused stencil: threads per CTA, 0..800 (0 = auto) */
   long long max_pairs;    /* dataset rows per member (0 = enough for
                              max_iters iterations)                          */
   int autotune;           /* 1: rnp_create times every launchable stencil
@@ -223,7 +223,8 @@ rnp_status rnp_randnet_predict(rnp_ctx* ctx, const double* q, double* out);
 rnp_status rnp_solve(rnp_ctx* ctx, const double* u0, double* U, rnp_stats* stats);
 
 /* Message of the last failed call on ctx ("" if none).  ctx may be NULL
- * for errors raised by rnp_create. */
+ * for errors raised by rnp_create and rnp_randnet_predict_noalloc: that
+ * message is kept per calling thread. */
 const char* rnp_last_error(const rnp_ctx* ctx);
 
 /* --- Alg. 1 one iteration at a time (continuous batching) --------------- */
@@ -282,8 +283,9 @@ rnp_status rnp_stencil_config(const rnp_ctx* ctx, int which, int* out);
  * the same prediction for one query without a context and calls no
  * allocating routine: the caller passes every input and the output, and the
  * intermediates (scaled query, features, distance partials, ridge weights)
- * live in one fixed file-scope device array of about 6.3 MB that every GPU
- * loading the library keeps until the process exits.
+ * live in one fixed file-scope device array of about 5.3 MB (660,518
+ * doubles for the limits below, plus 38 ints) that every GPU loading the
+ * library keeps until the process exits.
  *   prob       : only pde, grid, M, m and lambda are read.
  *   A, zeta    : device [M][d], [M]  random weights (e.g. rnp_get_weights).
  *   S, Y, Phi  : device [P][d], [P][d], [P][M]  scaled inputs
@@ -296,9 +298,10 @@ rnp_status rnp_stencil_config(const rnp_ctx* ctx, int which, int* out);
  *                is not finite (out is then 0 or not finite).
  * Limits: d <= 262144, P <= 4096, M <= 1024; larger sizes return RNP_EINVAL
  * before any work (message in rnp_last_error(NULL)).  Work is enqueued on
- * cuda_stream and the call returns without waiting.  The first call on a
- * device looks up the array's device address once (with that device
- * current); make that first call before any stream capture.  Every call on
+ * cuda_stream and the call returns without waiting.  Each call looks up the
+ * array's device address on the current device; the first call on a device
+ * also loads the library's device code there, so make that first call
+ * before any stream capture.  Every call on
  * a device shares the one array: calls whose work overlaps on the GPU (other
  * streams, other threads) race and must be serialised by the caller.     */
 rnp_status rnp_randnet_predict_noalloc(const rnp_problem* prob, const double* A,

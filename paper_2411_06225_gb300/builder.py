@@ -20,7 +20,8 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "librnp.so")
 SOURCES = ["api.cu", "stencil.cu", "randnet.cu", "noalloc.cu", "features_tc.cu"] + [
     f"stencil_{n}.cu" for n in ("burgers", "advect", "heat1", "heat2", "heat3",
-                                "diffreact", "bruss2", "bruss3", "swe", "swe_wall")]
+                                "diffreact", "bruss2", "bruss3", "swe", "swe_wall",
+                                "wide")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

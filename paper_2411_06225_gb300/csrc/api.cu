@@ -180,9 +180,9 @@ const char* validate(const rnp_problem* p) {
   if (p->precision != RNP_FP64 && p->precision != RNP_MIXED && p->precision != RNP_MIXED_BF16)
     return "unknown precision";
   if (p->exec != RNP_EXEC_FUSED && p->exec != RNP_EXEC_PLAIN) return "unknown exec";
-  if (p->cluster < 0 || p->cluster > 16 || p->threads < 0 || p->threads > 512 ||
+  if (p->cluster < 0 || p->cluster > 16 || p->threads < 0 || p->threads > 800 ||
       p->threads % 32)
-    return "cluster must be in [0,16] and threads a multiple of 32 in [0,512]";
+    return "cluster must be in [0,16] and threads a multiple of 32 in [0,800]";
   if (p->max_pairs < 0) return "max_pairs must be >= 0";
   return nullptr;
 }

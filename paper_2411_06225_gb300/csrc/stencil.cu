@@ -25,6 +25,7 @@
 // variants let the compiler contract multiply-adds.
 #include <cmath>
 #include <cstdio>
+#include <cstdarg>
 #include <cstring>
 
 #include "stencil_impl.cuh"
@@ -184,7 +185,7 @@ static bool x_shuffles(const Geom& g, int PX) {
   return w >= 1 && w <= 32 && (32 % w) == 0;
 }
 
-static FusedFn mixed_fn(int kp, int PX, int RS, bool XS, bool WALL, bool RK) {
+static FusedFn mixed_fn_narrow(int kp, int PX, int RS, bool XS, bool WALL, bool RK) {
   switch (kp) {
     case KP_BURGERS: return mixed_fn_burgers(PX, RS, XS, WALL, RK);
     case KP_ADVECT: return mixed_fn_advect(PX, RS, XS, WALL, RK);
@@ -197,6 +198,14 @@ static FusedFn mixed_fn(int kp, int PX, int RS, bool XS, bool WALL, bool RK) {
     case KP_SWE: return mixed_fn_swe(PX, RS, XS, WALL, RK);
   }
   return nullptr;
+}
+
+// The mixed kernel for a block of `threads`: blocks above 512 threads run
+// the wide instantiation (80 registers per thread).
+static FusedFn mixed_fn(int kp, int PX, int RS, bool XS, bool WALL, bool RK, int threads) {
+  if (threads > 512)
+    return threads <= kWideThreads ? mixed_wide_fn(kp, PX, RS, XS, WALL, RK) : nullptr;
+  return mixed_fn_narrow(kp, PX, RS, XS, WALL, RK);
 }
 
 static const int kRs[] = {1, 2, 4, 8, 16};
@@ -212,10 +221,27 @@ static size_t smem_bytes(const Geom& g, bool fp32, int CS) {
   const long long ncell = (long long)(g.outer / CS) * g.plane;
   // FP64 kernel: two stage buffers; mixed kernel: two stage buffers with two
   // ghost rows each, the low words, then two mbarriers, the 16-byte halo
-  // target table and two abort flags
+  // target table, two abort flags, the neighbours' two stop stages and the
+  // tensor-memory base (64 bytes)
   if (!fp32) return 2 * (size_t)g.ncomp * ncell * 8;
   const size_t f = (2 * (size_t)g.ncomp * (ncell + 2 * g.plane) + (size_t)g.ncomp * ncell) * 4;
-  return ((f + 15) & ~(size_t)15) + 48;
+  return ((f + 15) & ~(size_t)15) + 64;
+}
+
+// Why the configurations tried were not launchable (for error messages):
+// the first reasons of the current pick, appended.
+static thread_local char g_unlaunchable[384] = "";
+static void note_unlaunchable(const char* fmt, ...) __attribute__((format(printf, 1, 2)));
+static void note_unlaunchable(const char* fmt, ...) {
+  const size_t n = strlen(g_unlaunchable);
+  if (n + 8 >= sizeof(g_unlaunchable)) return;
+  char* p = g_unlaunchable + n;
+  size_t left = sizeof(g_unlaunchable) - n;
+  if (n) { snprintf(p, left, "; "); p += 2; left -= 2; }
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(p, left, fmt, ap);
+  va_end(ap);
 }
 
 static bool launchable(FusedFn fn, int CS, int threads, size_t smem, int nitems) {
@@ -223,21 +249,44 @@ static bool launchable(FusedFn fn, int CS, int threads, size_t smem, int nitems)
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
           cudaSuccess) {
+    note_unlaunchable("no current device");
     cudaGetLastError();
     return false;
   }
-  if ((long long)smem > optin) return false;
+  // the kernel's static shared memory (the wide kernel's tensor-memory base)
+  // comes out of the same per-block limit as the dynamic part
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, (const void*)fn) != cudaSuccess) {
+    cudaGetLastError();
+    note_unlaunchable("no attributes for the kernel");
+    return false;
+  }
+  const int dyn_max = optin - (int)fa.sharedSizeBytes;
+  if ((long long)smem > dyn_max) {
+    note_unlaunchable("%zu B of shared memory > %d", smem, dyn_max);
+    return false;
+  }
+  if (threads > fa.maxThreadsPerBlock) {
+    note_unlaunchable("%d threads > %d per block for this kernel (%d registers)", threads,
+                      fa.maxThreadsPerBlock, fa.numRegs);
+    return false;
+  }
   // The limit is a per-function attribute shared by every configuration that
   // maps to this instantiation, so it is raised to the device maximum once
   // rather than set to this configuration's size.
-  if (cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           optin) != cudaSuccess) {
+  cudaError_t e = cudaFuncSetAttribute((const void*)fn,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
+  if (e != cudaSuccess) {
+    note_unlaunchable("shared-memory attribute: %s",
+             cudaGetErrorString(e));
     cudaGetLastError();
     return false;
   }
   if (CS > 8 &&
-      cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeNonPortableClusterSizeAllowed,
-                           1) != cudaSuccess) {
+      (e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                                1)) != cudaSuccess) {
+    note_unlaunchable("cluster-size attribute: %s",
+             cudaGetErrorString(e));
     cudaGetLastError();
     return false;
   }
@@ -253,10 +302,15 @@ static bool launchable(FusedFn fn, int CS, int threads, size_t smem, int nitems)
   lc.attrs = at;
   lc.numAttrs = 1;
   int nclusters = 0;
-  if (cudaOccupancyMaxActiveClusters(&nclusters, (const void*)fn, &lc) != cudaSuccess) {
+  if ((e = cudaOccupancyMaxActiveClusters(&nclusters, (const void*)fn, &lc)) != cudaSuccess) {
+    note_unlaunchable("occupancy query: %s",
+             cudaGetErrorString(e));
     cudaGetLastError();
     return false;
   }
+  if (nclusters < 1)
+    note_unlaunchable("no cluster of %d CTAs x %d threads with %zu B of shared memory fits", CS,
+             threads, smem);
   return nclusters >= 1;
 }
 
@@ -287,12 +341,16 @@ static bool try_cfg(const Geom& g, bool fp32, int CS, int threads, int nitems,
         if (g_tile_relax == 2) budget = 40;
         if (RS * g.ncomp * PX > budget) continue;
         const long long t = tiles * (nloc / RS);
-        if (t > 512 || t < 1) continue;
+        if (t > kWideThreads || t < 1) continue;
+        // the wide kernel's tensor-memory accesses are warp-collective: whole
+        // warps only
+        if (t > 512 && t % 32) continue;
         if (threads > 0 && t != threads) continue;
         // the RK4 and the Euler instantiation of this tile (the RK4 one is
-        // the larger: it decides launchability)
-        FusedFn fn = mixed_fn(g.kp, PX, RS, x_shuffles(g, PX), g.bc != 0, true);
-        FusedFn fe = mixed_fn(g.kp, PX, RS, x_shuffles(g, PX), g.bc != 0, false);
+        // the larger: it decides launchability); blocks above 512 threads
+        // exist only as the wide kernel's tiles
+        FusedFn fn = mixed_fn(g.kp, PX, RS, x_shuffles(g, PX), g.bc != 0, true, (int)t);
+        FusedFn fe = mixed_fn(g.kp, PX, RS, x_shuffles(g, PX), g.bc != 0, false, (int)t);
         if (!fn || !fe || !launchable(fn, CS, (int)t, smem, nitems) ||
             !launchable(fe, CS, (int)t, smem, nitems))
           continue;
@@ -353,6 +411,7 @@ static bool pick_one(const Geom& g, bool fp32, int nitems, bool latency, int wan
 
 bool pick_stencil(const Geom& g, bool fp32, int nitems, bool latency, int want_cluster,
                   int want_threads, StencilCfg* out, char* why, int why_len, bool rk8) {
+  g_unlaunchable[0] = 0;
   if (rk8) return pick_one(g, false, nitems, latency, want_cluster, want_threads, out, why,
                            why_len, true);
   // a mixed-precision context prefers an FP32 tile at any cluster size and
@@ -377,8 +436,8 @@ static bool pick_one(const Geom& g, bool fp32, int nitems, bool latency, int wan
                      int want_threads, StencilCfg* out, char* why, int why_len, bool rk8) {
   if (want_cluster > 0) {
     if (try_cfg(g, fp32, want_cluster, want_threads, nitems, out, 0, 0, rk8)) return true;
-    snprintf(why, why_len, "stencil configuration cluster=%d threads=%d is not launchable",
-             want_cluster, want_threads);
+    snprintf(why, why_len, "stencil configuration cluster=%d threads=%d is not launchable (%s)",
+             want_cluster, want_threads, g_unlaunchable[0] ? g_unlaunchable : "no tile of that size");
     return false;
   }
   // every cluster size up to 16 that divides the split axis; the smallest
@@ -425,26 +484,34 @@ static bool pick_one(const Geom& g, bool fp32, int nitems, bool latency, int wan
 int list_stencil_cfgs(const Geom& g, bool fp32, int nitems, StencilCfg* out, int maxn,
                       bool rk8) {
   int n = 0;
-  for (int CS = 1; CS <= 16 && n < maxn; ++CS) {
-    if (g.outer % CS) continue;
-    if (fp32) {
-      // every spill-free FP32 tile at this cluster size
-      const int pxs[] = {2, 4};
-      const int rss[] = {1, 2, 4, 5, 8};
-      for (int PX : pxs)
-        for (int RS : rss) {
-          if (n >= maxn) break;
-          if (g.nx % PX || (g.outer / CS) % RS) continue;
-          const long long t = (g.plane / PX) * ((g.outer / CS) / RS);
-          StencilCfg c;
-          if (t >= 32 && t <= 512 && try_cfg(g, true, CS, (int)t, nitems, &c, PX, RS))
-            out[n++] = c;
-        }
-    } else {
-      StencilCfg c;
-      if (try_cfg(g, false, CS, 0, nitems, &c, 0, 0, rk8)) out[n++] = c;
+  // FP32: the spill-free tiles; where fewer than three exist (slices whose
+  // CTA share leaves little room), also the wide and the register-tight
+  // tiles, level by level, so that the timing decides between them
+  for (int level = 0; level <= (fp32 ? 2 : 0); ++level) {
+    g_tile_relax = level;
+    n = 0;
+    for (int CS = 1; CS <= 16 && n < maxn; ++CS) {
+      if (g.outer % CS) continue;
+      if (fp32) {
+        const int pxs[] = {2, 4};
+        const int rss[] = {1, 2, 4, 5, 8};
+        for (int PX : pxs)
+          for (int RS : rss) {
+            if (n >= maxn) break;
+            if (g.nx % PX || (g.outer / CS) % RS) continue;
+            const long long t = (g.plane / PX) * ((g.outer / CS) / RS);
+            StencilCfg c;
+            if (t >= 32 && t <= kWideThreads && try_cfg(g, true, CS, (int)t, nitems, &c, PX, RS))
+              out[n++] = c;
+          }
+      } else {
+        StencilCfg c;
+        if (try_cfg(g, false, CS, 0, nitems, &c, 0, 0, rk8)) out[n++] = c;
+      }
     }
+    if (n >= 3) break;
   }
+  g_tile_relax = 0;
   return n;
 }
 
@@ -457,7 +524,7 @@ cudaError_t launch_stencil_fused(const Geom& g, const Coef& c, bool fp32, int sc
   const bool use_mixed = fp32 && cfg.px > 0;
   if (scheme == SCHEME_RK8 && use_mixed) return cudaErrorInvalidValue;  // FP64 only
   FusedFn fn = use_mixed ? mixed_fn(g.kp, cfg.px, cfg.rs, x_shuffles(g, cfg.px), g.bc != 0,
-                                    scheme == SCHEME_RK4)
+                                    scheme == SCHEME_RK4, cfg.threads)
                : scheme == SCHEME_RK8 ? fused_rk8_fn(g.kp, cfg.R)
                                       : fused_fn(g.kp, cfg.R);
   if (!fn) return cudaErrorInvalidValue;

@@ -689,6 +689,25 @@ __device__ __forceinline__ bool halo_wait(uint32_t mbar, uint32_t parity) {
   return false;
 }
 
+// Whether the phase of the given parity has completed (no wait).
+__device__ __forceinline__ bool mbar_done(uint32_t mbar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n"
+      " mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Counts bytes that will never arrive as received, so that the phase can
+// complete on the bytes that were sent.
+__device__ __forceinline__ void mbar_complete(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.complete_tx.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(bytes)
+               : "memory");
+}
+
 // Where a stage sends its edge rows: outer row 0 to the previous rank's
 // ghost row nloc, outer row nloc - 1 to the next rank's ghost row -1, both
 // in the buffer of the next stage's parity (with no-flux walls the first and
@@ -752,11 +771,63 @@ __device__ __forceinline__ void push_edge_q(const HaloOut& h, bool to_prev, uint
   push_edge<PX>(h, to_prev, elem, v);
 }
 
-template <int KP, int PX, int RS, int STAGE, bool XS, bool WALL>
+// --- tensor memory as per-thread storage -------------------------------
+// The wide 3D kernel keeps each thread's step state uh and Runge-Kutta
+// accumulator in tensor memory (TMEM, 256 KB per SM, otherwise unused by
+// the stencil) instead of registers: warp w reaches TMEM lanes
+// 32 (w % 4) .. 32 (w % 4) + 31 (its lane quadrant), thread i of the warp
+// lane 32 (w % 4) + i, and the warps sharing a quadrant use disjoint column
+// ranges.  tcgen05.ld / tcgen05.st move N consecutive 32-bit columns of the
+// thread's own lane; both are warp-collective and asynchronous
+// (tcgen05.wait::ld before the loaded registers are used, tcgen05.wait::st
+// before the columns are read again).  Only N = 4 and 8 are used.
+template <int N>
+__device__ __forceinline__ void tm_ld(uint32_t taddr, float* v) {
+  uint32_t r[N];
+  if constexpr (N == 4)
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(taddr));
+  else
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < N; ++i) v[i] = __uint_as_float(r[i]);
+}
+template <int N>
+__device__ __forceinline__ void tm_st(uint32_t taddr, const float* v) {
+  if constexpr (N == 4)
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr),
+                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])),
+                 "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3]))
+                 : "memory");
+  else
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(
+                     taddr),
+                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])),
+                 "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+                 "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+                 "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+                 : "memory");
+}
+// Waits for this thread's TMEM loads; the registers pass through the asm so
+// that no use of them is scheduled before the wait.
+template <int N>
+__device__ __forceinline__ void tm_wait_ld(float* v) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < N; ++i) asm volatile("" : "+f"(v[i]));
+}
+__device__ __forceinline__ void tm_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+template <int KP, int PX, int RS, int STAGE, bool XS, bool WALL, bool TM>
 __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* __restrict__ B,
                                             float* __restrict__ Bn, float* ulo,
                                             float (&uh)[RS][KT<KP>::NC][PX],
-                                            float (&acc)[RS][KT<KP>::NC][PX],
+                                            float (&acc)[RS][KT<KP>::NC][PX], uint32_t tm,
                                             int ncell, int plane, int nloc, int ofirst, int dir,
                                             int rowoff, int woff, int eoff, int yn_off, int ys_off,
                                             bool euler, const HaloOut& ho, unsigned xmask,
@@ -785,10 +856,26 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
     ld_vec<PX>(row, cur[q]);
     if (DIMS >= 2) ld_vec<PX>(row - rstep, back[q]);
   }
-#pragma unroll
+  // (TM: the rows' state is addressed in tensor memory, so the row loop can
+  // stay rolled, which keeps one row's values live at a time)
+#pragma unroll (TM ? 1 : RS)
   for (int r = 0; r < RS; ++r) {
     const int o = ofirst + dir * r;
     const int cb = o * plane + rowoff;    // first cell of this tile row
+    // this row's step state and accumulator: the register tile's row, or
+    // (TM) a copy loaded from tensor memory (columns r NC PX .. of the
+    // thread's uh block, then of its accumulator block RS NC PX further)
+    float ur[NC][PX], ar[NC][PX];
+    if constexpr (TM) {
+      tm_ld<NC * PX>(tm + (uint32_t)(r * NC * PX), &ur[0][0]);
+      if (!euler && STAGE > 0) {
+        tm_ld<NC * PX>(tm + (uint32_t)((RS + r) * NC * PX), &ar[0][0]);
+        tm_wait_ld<NC * PX>(&ar[0][0]);
+      }
+      tm_wait_ld<NC * PX>(&ur[0][0]);
+    }
+    float (&U_)[NC][PX] = TM ? ur : uh[r];
+    float (&A_)[NC][PX] = TM ? ar : acc[r];
 #pragma unroll
     for (int q = 0; q < NC; ++q)
       if (DIMS >= 2) ld_vec<PX>(B + q * ncell + cb + rstep, ahead[q]);
@@ -882,7 +969,7 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
         }
 #pragma unroll
         for (int q = 0; q < NC; ++q) {
-          float2 U = pk(uh[r][q][p0], uh[r][q][p1]);
+          float2 U = pk(U_[q][p0], U_[q][p1]);
           float2 w;
           if (euler) {
             float2 l = *reinterpret_cast<const float2*>(ulo + q * ncl + cb + p0);
@@ -890,20 +977,20 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
             *reinterpret_cast<float2*>(ulo + q * ncl + cb + p0) = l;
             w = U;
           } else if (STAGE == 0) {
-            acc[r][q][p0] = kq[q].x; acc[r][q][p1] = kq[q].y;
+            A_[q][p0] = kq[q].x; A_[q][p1] = kq[q].y;
             w = fma2(pk1(h2), kq[q], U);
           } else if (STAGE == 1 || STAGE == 2) {
-            const float2 A2 = fma2(pk1(2.f), kq[q], pk(acc[r][q][p0], acc[r][q][p1]));
-            acc[r][q][p0] = A2.x; acc[r][q][p1] = A2.y;
+            const float2 A2 = fma2(pk1(2.f), kq[q], pk(A_[q][p0], A_[q][p1]));
+            A_[q][p0] = A2.x; A_[q][p1] = A2.y;
             w = fma2(pk1(STAGE == 1 ? h2 : dt), kq[q], U);
           } else {
-            const float2 A2 = add2(pk(acc[r][q][p0], acc[r][q][p1]), kq[q]);
+            const float2 A2 = add2(pk(A_[q][p0], A_[q][p1]), kq[q]);
             float2 l = *reinterpret_cast<const float2*>(ulo + q * ncl + cb + p0);
             two_sum_acc2(U, l, mul2(pk1(h6), A2));
             *reinterpret_cast<float2*>(ulo + q * ncl + cb + p0) = l;
             w = U;
           }
-          uh[r][q][p0] = U.x; uh[r][q][p1] = U.y;
+          U_[q][p0] = U.x; U_[q][p1] = U.y;
           wout[q][p0] = w.x; wout[q][p1] = w.y;
         }
       }
@@ -935,28 +1022,34 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
           float w;
           if (euler) {
             float l = ulo[q * ncl + cb + p];
-            two_sum_acc(uh[r][q][p], l, __fmul_rn(dt, k[q]));
+            two_sum_acc(U_[q][p], l, __fmul_rn(dt, k[q]));
             ulo[q * ncl + cb + p] = l;
-            w = uh[r][q][p];
+            w = U_[q][p];
           } else if (STAGE == 0) {
-            acc[r][q][p] = k[q];
-            w = uh[r][q][p] + h2 * k[q];
+            A_[q][p] = k[q];
+            w = U_[q][p] + h2 * k[q];
           } else if (STAGE == 1) {
-            acc[r][q][p] = acc[r][q][p] + 2.f * k[q];
-            w = uh[r][q][p] + h2 * k[q];
+            A_[q][p] = A_[q][p] + 2.f * k[q];
+            w = U_[q][p] + h2 * k[q];
           } else if (STAGE == 2) {
-            acc[r][q][p] = acc[r][q][p] + 2.f * k[q];
-            w = uh[r][q][p] + dt * k[q];
+            A_[q][p] = A_[q][p] + 2.f * k[q];
+            w = U_[q][p] + dt * k[q];
           } else {
-            const float a = acc[r][q][p] + k[q];
+            const float a = A_[q][p] + k[q];
             float l = ulo[q * ncl + cb + p];
-            two_sum_acc(uh[r][q][p], l, __fmul_rn(h6, a));
+            two_sum_acc(U_[q][p], l, __fmul_rn(h6, a));
             ulo[q * ncl + cb + p] = l;
-            w = uh[r][q][p];
+            w = U_[q][p];
           }
           wout[q][p] = w;
         }
       }
+    }
+    if constexpr (TM) {
+      // the state changes in Euler steps and the last RK stage, the
+      // accumulator in the first three RK stages
+      if (euler || STAGE == 3) tm_st<NC * PX>(tm + (uint32_t)(r * NC * PX), &ur[0][0]);
+      else tm_st<NC * PX>(tm + (uint32_t)((RS + r) * NC * PX), &ar[0][0]);
     }
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
@@ -973,12 +1066,17 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
       }
     }
   }
+  if constexpr (TM) tm_wait_st();
 }
 
 // RK: the fine solver's RK4 (true) or the coarse forward Euler (false), one
 // instantiation each, so the RK4 kernel carries no Euler code (registers).
-template <int KP, int PX, int RS, bool XS, bool WALL, bool RK>
-__global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant__ FusedParams P) {
+// The body is shared by two kernels: k_stencil_mixed (up to 512 threads,
+// 128 registers each) and k_stencil_mixed_wide (up to 800 threads capped at
+// 80 registers, for slices whose CTA share leaves one CTA per SM: there the
+// wider block holds twice the warps and a smaller register tile per thread).
+template <int KP, int PX, int RS, bool XS, bool WALL, bool RK, bool TM>
+__device__ __forceinline__ void mixed_body(const FusedParams& P) {
   constexpr int NC = KT<KP>::NC, DIMS = KT<KP>::DIMS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int CS = P.cluster;
@@ -996,7 +1094,8 @@ __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant_
   float* const buf0 = reinterpret_cast<float*>(smem_raw) + plane;   // row 0 of buffer 0
   float* const buf1 = buf0 + NC * ncell;
   float* const ulo = reinterpret_cast<float*>(smem_raw) + 2 * NC * ncell;
-  // (P.moff = the 16-byte aligned end of the buffers: 4 (2 NC ncell + NC ncl))
+  // (P.moff = the 16-byte aligned end of the buffers: 4 (2 NC ncell + NC ncl);
+  // after it 64 bytes: mbarriers, target table, flags, stop stages, TMEM base)
   uint64_t* const mbar = reinterpret_cast<uint64_t*>(smem_raw + P.moff);
   const bool remote = DIMS >= 2 && CS > 1;
   const uint32_t sbase = cta_smem_u32(smem_raw);
@@ -1043,6 +1142,9 @@ __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant_
   // last row the next rank's ghost row -1 (buffer 0; +boff for buffer 1)
   uint4* const tab = reinterpret_cast<uint4*>(mbar + 2);
   volatile int* const abort_flag = reinterpret_cast<volatile int*>(tab + 1);  // [2]
+  // the stop stages of the previous and the next rank (written by them);
+  // after them 16 bytes for the tensor-memory base (wide kernel)
+  volatile int* const stop_in = abort_flag + 2;  // [2]
   // With no-flux walls the first rank's row 0 fills its own S ghost row and
   // the last rank's last row its own N ghost row (local stores, no mbarrier:
   // a zero mbarrier address in the table marks a local target).
@@ -1094,9 +1196,33 @@ __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant_
         buf0[q * ncell + o * plane + rowoff + p] = h;
         ulo[q * ncl + o * plane + rowoff + p] = (float)(v - (double)h);
       }
+  // TM: 256 TMEM columns for the CTA (at most 8 warps share a lane
+  // quadrant, each using 2 RS NC PX <= 32 columns), allocated by warp 0;
+  // the allocation writes the base address to tm_base
+  volatile uint32_t* const tm_base = reinterpret_cast<volatile uint32_t*>(stop_in + 2);
+  if constexpr (TM) {
+    if (threadIdx.x < 32) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
+                       cta_smem_u32(const_cast<uint32_t*>(tm_base)))
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
   // every CTA's mbarriers and target table are initialised before anyone
   // pushes
   if (CS > 1) cg::this_cluster().sync(); else __syncthreads();
+  // this thread's TMEM columns: lane quadrant of its warp, column block of
+  // its warp among those sharing the quadrant
+  uint32_t tm = 0;
+  if constexpr (TM) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t w = threadIdx.x >> 5;
+    tm = *tm_base + ((32u * (w & 3u)) << 16) + (w >> 2) * (uint32_t)(2 * RS * NC * PX);
+#pragma unroll
+    for (int r = 0; r < RS; ++r) tm_st<NC * PX>(tm + (uint32_t)(r * NC * PX), &uh[r][0][0]);
+    tm_wait_st();
+  }
   // stage 0's halo: the initial edge rows
   if (DIMS >= 2) {
     const HaloOut h0 = halo_out(0, true);
@@ -1116,63 +1242,142 @@ __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant_
   }
 
   // Stage s reads buffer s & 1 (with its ghost rows) and writes buffer
-  // (s + 1) & 1 and the neighbours' ghost rows of that buffer.  At the start
-  // of stage s thread 0 arms mbarrier s & 1 for the ghost-row bytes, and the
-  // threads that read ghost rows (those owning an edge row) wait for its
-  // phase, parity (s >> 1) & 1, with cluster-scope acquire; the other warps
-  // start computing at once.
+  // (s + 1) & 1 and the neighbours' ghost rows of that buffer.  The ghost
+  // rows of stage s are pushed by the neighbours during their stage s - 1
+  // (stage 0's before the loop) and complete bytes on mbarrier s & 1, in
+  // its phase of parity (s >> 1) & 1.  Thread 0 arms that phase one stage
+  // ahead, at the start of stage s - 1 (the mbarrier's previous phase, stage
+  // s - 2, completed before stage s - 2 began), and the threads that read
+  // ghost rows (those owning an edge row) wait for it at the end of stage
+  // s - 1, with cluster-scope acquire, before the CTA barrier that closes
+  // the stage.  A CTA whose wait gave up therefore stops before computing
+  // stage s and pushes no further rows.  Since a CTA computes stage s only
+  // after both neighbours' stage-s rows arrived, i.e. after both neighbours
+  // computed stage s - 1, the stop stages of adjacent CTAs differ by at most
+  // one, which bounds what can still be in flight (the drain below).
   const int nst = RK ? 4 * P.steps : P.steps;
-  auto stage_begin = [&](int s) {
-    if (!remote) return;
-    if (threadIdx.x == 0) mbar_expect(mb0 + 8u * (s & 1), tx_bytes);
-    if (edge && !halo_wait(mb0 + 8u * (s & 1), (uint32_t)((s >> 1) & 1))) {
+  auto arm = [&](int s) {
+    if (remote && s < nst && threadIdx.x == 0) mbar_expect(mb0 + 8u * (s & 1), tx_bytes);
+  };
+  auto wait_rows = [&](int s) {
+    if (remote && s < nst && edge && !halo_wait(mb0 + 8u * (s & 1), (uint32_t)((s >> 1) & 1))) {
       abort_flag[s & 1] = 1;
       if (P.err) atomicExch(P.err, 1);
     }
   };
-  // CTA barrier closing stage s; true when a wait of stage s gave up.  The
-  // flag of stage s is written before this barrier and read after it; the
-  // next write to it (stage s + 2) comes after the barrier of stage s + 1,
-  // so every thread reads the same value and leaves at the same stage.
-  auto stage_end = [&](int s) {
+  // CTA barrier before stage s; true when a wait for the ghost rows of
+  // stage s gave up.  The flag of stage s is written before this barrier
+  // and read after it; the next write to it (stage s + 2) comes after the
+  // barrier before stage s + 1, so every thread reads the same value and
+  // stops at the same stage.
+  auto gate = [&](int s) {
     __syncthreads();
     return abort_flag[s & 1] != 0;
   };
 #define RNP_MIXED_STAGE(STG, BIN, BOUT, PAR, ON, EUL)                                          \
-  mixed_stage<KP, PX, RS, STG, XS, WALL>(P, BIN, BOUT, ulo, uh, acc, ncell, plane, nloc,      \
+  mixed_stage<KP, PX, RS, STG, XS, WALL, TM>(P, BIN, BOUT, ulo, uh, acc, tm, ncell, plane, nloc, \
                                          ofirst, dir, rowoff, woff, eoff, yn_off, ys_off,    \
                                          EUL, halo_out((PAR) ^ 1, ON), xmask, xsw, xwest,    \
                                          xeast, xlo, xhi, bth)
 
+  // first stage this CTA did not compute (nst: it computed them all)
+  int stop = nst;
+  arm(0);
   __syncthreads();
-  for (int step = 0; step < P.steps; ++step) {
+  wait_rows(0);
+  if (gate(0)) stop = 0;
+  for (int step = 0; step < P.steps && stop == nst; ++step) {
     if constexpr (RK) {
       const int s0 = 4 * step;
-      stage_begin(s0);
+      arm(s0 + 1);
       RNP_MIXED_STAGE(0, buf0, buf1, 0, true, false);
-      if (stage_end(s0)) break;
-      stage_begin(s0 + 1);
+      wait_rows(s0 + 1);
+      if (gate(s0 + 1)) { stop = s0 + 1; break; }
+      arm(s0 + 2);
       RNP_MIXED_STAGE(1, buf1, buf0, 1, true, false);
-      if (stage_end(s0 + 1)) break;
-      stage_begin(s0 + 2);
+      wait_rows(s0 + 2);
+      if (gate(s0 + 2)) { stop = s0 + 2; break; }
+      arm(s0 + 3);
       RNP_MIXED_STAGE(2, buf0, buf1, 0, true, false);
-      if (stage_end(s0 + 2)) break;
-      stage_begin(s0 + 3);
+      wait_rows(s0 + 3);
+      if (gate(s0 + 3)) { stop = s0 + 3; break; }
+      arm(s0 + 4);
       RNP_MIXED_STAGE(3, buf1, buf0, 1, s0 + 4 < nst, false);
-      if (stage_end(s0 + 3)) break;
+      wait_rows(s0 + 4);
+      if (gate(s0 + 4)) { stop = s0 + 4; break; }
     } else {
       // forward Euler: buffers alternate every step
-      stage_begin(step);
+      arm(step + 1);
       if ((step & 1) == 0)
         RNP_MIXED_STAGE(0, buf0, buf1, 0, step + 1 < nst, true);
       else
         RNP_MIXED_STAGE(0, buf1, buf0, 1, step + 1 < nst, true);
-      if (stage_end(step)) break;
+      wait_rows(step + 1);
+      if (gate(step + 1)) { stop = step + 1; break; }
     }
   }
 #undef RNP_MIXED_STAGE
-  // no CTA leaves while a neighbour may still address its shared memory
+  // Drain: no CTA leaves while a ghost-row store aimed at it may be in
+  // flight.  Every CTA publishes its stop stage to both neighbours; after
+  // the cluster barrier nobody pushes any more.  A neighbour with stop
+  // stage sn sent the rows of every stage t <= sn (t < nst).  Pending at
+  // this CTA are at most the armed phase of stage `stop` (bytes of a
+  // neighbour that stopped earlier never come: they are counted as received)
+  // and the unarmed phase of stage stop + 1 (armed now for the bytes of the
+  // neighbours that computed stage `stop`); nothing of a later stage can
+  // have been sent.  Thread 0 waits (bounded) for both, then the cluster
+  // barrier below lets every CTA leave.  With no timeout anywhere every
+  // stop stage is nst and nothing is pending.
+  if (remote) {
+    if (threadIdx.x == 0) {
+      cg::cluster_group cl = cg::this_cluster();
+      volatile int* to_prev = cl.map_shared_rank(const_cast<int*>(stop_in) + 1, (rank + CS - 1) % CS);
+      volatile int* to_next = cl.map_shared_rank(const_cast<int*>(stop_in), (rank + 1) % CS);
+      *to_prev = stop;
+      *to_next = stop;
+    }
+    cg::this_cluster().sync();
+    if (threadIdx.x == 0) {
+      const int sp = wall_lo ? nst : stop_in[0];
+      const int sn = wall_hi ? nst : stop_in[1];
+      const uint32_t row = (uint32_t)(NC * plane * 4);
+      bool ok = true;
+      if (stop < nst) {
+        const uint32_t mb = mb0 + 8u * (stop & 1), par = (uint32_t)((stop >> 1) & 1);
+        if (!mbar_done(mb, par)) {
+          const uint32_t missing = (!wall_lo && sp < stop ? row : 0u) +
+                                   (!wall_hi && sn < stop ? row : 0u);
+          if (missing) mbar_complete(mb, missing);
+          ok = halo_wait(mb, par);
+        }
+      }
+      if (stop + 1 < nst) {
+        const uint32_t sent = (!wall_lo && sp > stop ? row : 0u) +
+                              (!wall_hi && sn > stop ? row : 0u);
+        if (sent) {
+          const uint32_t mb = mb0 + 8u * ((stop + 1) & 1);
+          mbar_expect(mb, sent);
+          ok = halo_wait(mb, (uint32_t)(((stop + 1) >> 1) & 1)) && ok;
+        }
+      }
+      if (!ok && P.err) atomicExch(P.err, 1);
+    }
+  }
   if (CS > 1) cg::this_cluster().sync();
+  if constexpr (TM) {
+    // the final state back from tensor memory, then the columns released
+#pragma unroll
+    for (int r = 0; r < RS; ++r) {
+      tm_ld<NC * PX>(tm + (uint32_t)(r * NC * PX), &uh[r][0][0]);
+      tm_wait_ld<NC * PX>(&uh[r][0][0]);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (threadIdx.x < 32)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(*tm_base)
+                   : "memory");
+  }
   double* out = P.out + item_off(P.it.dst_off, P.it.dst_base, P.it.dst_stride, item) + base;
   double* out2 = P.out2 ? P.out2 + item_off(P.it.dst2_off, P.it.dst2_base, P.it.dst2_stride, item) + base
                         : nullptr;
@@ -1187,6 +1392,25 @@ __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant_
         out[q * P.n + o * plane + rowoff + p] = v;
         if (out2) out2[q * P.n + o * plane + rowoff + p] = v;
       }
+}
+
+template <int KP, int PX, int RS, bool XS, bool WALL, bool RK>
+__global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant__ FusedParams P) {
+  mixed_body<KP, PX, RS, XS, WALL, RK, false>(P);
+}
+
+// Registers per thread of the wide kernel.  The register file is split
+// evenly over the SM's four schedulers (16384 each) and a block's warps are
+// dealt out among them, so 25 warps put 7 on one scheduler: 7 x 32 x 72 =
+// 16128 registers fit, 80 would not.  Blocks of up to 800 threads launch.
+static constexpr int kWideRegs = 72;
+static constexpr int kWideThreads = 800;
+
+// The wide kernel keeps the step state and the accumulator in tensor memory
+// (TM), which leaves the registers to the stencil's working rows.
+template <int KP, int PX, int RS, bool XS, bool WALL, bool RK>
+__global__ void __maxnreg__(kWideRegs) k_stencil_mixed_wide(const __grid_constant__ FusedParams P) {
+  mixed_body<KP, PX, RS, XS, WALL, RK, true>(P);
 }
 
 typedef void (*FusedFn)(const FusedParams);
@@ -1253,6 +1477,22 @@ inline FusedFn mixed_for(int PX, int RS, bool XS, bool WALL, bool RK) {
   if (PX == 4) return RK ? mixed_for_wall<KP, 4, true>(RS, XS, WALL) : mixed_for_wall<KP, 4, false>(RS, XS, WALL);
   return nullptr;
 }
+
+// The wide kernel's instantiations: tiles of at most 16 state values per
+// thread, periodic, x neighbours from shared memory (the configurations a
+// wide block is picked for: a slice whose CTA share fills the shared memory).
+template <int KP, bool RK>
+inline FusedFn mixed_wide_for(int PX, int RS) {
+  if (PX == 2 && RS == 1) return k_stencil_mixed_wide<KP, 2, 1, false, false, RK>;
+  if (PX == 2 && RS == 2) return k_stencil_mixed_wide<KP, 2, 2, false, false, RK>;
+  if (PX == 2 && RS == 4) return k_stencil_mixed_wide<KP, 2, 4, false, false, RK>;
+  if (PX == 4 && RS == 1) return k_stencil_mixed_wide<KP, 4, 1, false, false, RK>;
+  if (PX == 4 && RS == 2) return k_stencil_mixed_wide<KP, 4, 2, false, false, RK>;
+  return nullptr;
+}
+// defined in stencil_wide.cu: the 3D Brusselator's wide kernels (nullptr
+// for other operators and tiles)
+FusedFn mixed_wide_fn(int kp, int PX, int RS, bool XS, bool WALL, bool RK);
 
 // Per-PDE entry points, defined in stencil_<pde>.cu.
 #define RNP_STENCIL_DECL(NAME)                 \

@@ -1,0 +1,17 @@
+// stencil_wide.cu -- instantiations of the wide mixed-precision stencil
+// kernel (up to 800 threads per CTA at 80 registers), kept apart so the
+// build runs in parallel with the other operators.
+#include "stencil_impl.cuh"
+
+namespace rnp {
+
+FusedFn mixed_wide_fn(int kp, int PX, int RS, bool XS, bool WALL, bool RK) {
+  if (XS || WALL) return nullptr;
+  switch (kp) {
+    case KP_BRUSS3: return RK ? mixed_wide_for<KP_BRUSS3, true>(PX, RS)
+                              : mixed_wide_for<KP_BRUSS3, false>(PX, RS);
+  }
+  return nullptr;
+}
+
+}  // namespace rnp
