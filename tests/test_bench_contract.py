@@ -13,7 +13,7 @@ def bench_mod(monkeypatch):
     import bench
     calls = []
 
-    def fake_baseline(seconds_hint=20.0):
+    def fake_baseline(name=None):
         calls.append(1)
         return {"value": 1.0e8 + len(calls), "unit": bench.UNIT, "cores": 4, "kind": "oracle",
                 "sample": "stub sample"}
@@ -44,18 +44,42 @@ def test_reference_line(bench_mod, capsys, monkeypatch):
     assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT,
                            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert line["higher_is_better"] is True and line["vs_baseline"] is None
-    assert line["config"]["grid"] == "128x128x2" and line["config"]["N"] == 64
-    assert line["config"]["nF"] == 1000 and "diffreact2d" in line["config"]["workload"]
+    # the headline workload, with the same config object as the GPU arm's
+    assert line["config"]["grid"] == "40x40x40x2" and line["config"]["N"] == 256
+    assert line["config"]["nF"] == 1000 and line["config"]["batch"] == 8
+    assert "bruss3d" in line["config"]["workload"]
+    assert line["config"] == bench.line_config("bruss3d", "mixed", 1)
 
 
 def test_reference_line_names_its_workload(bench_mod, capsys, monkeypatch):
     bench, calls = bench_mod
     monkeypatch.delenv("RANK", raising=False)
-    monkeypatch.setattr(bench, "WORKLOAD", "swe_box")
-    assert bench.run_reference(_args(1, 0)) == 0
+    args = _args(1, 0)
+    args.workload = "swe_box"
+    assert bench.run_reference(args) == 0
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert line["config"]["grid"] == "100x50x3" and line["config"]["N"] == 235
     assert line["config"]["nF"] == 35 and "walls" in line["config"]["workload"]
+    assert line["config"] == bench.line_config("swe_box", "mixed", 1)
+
+
+def test_cpu_sample_keeps_the_slice_length():
+    """The oracle's bounded sample: the workload's grid, operator and slice
+    length, one member, at most 16 slices and 2e9 cell-updates per
+    iteration."""
+    import bench
+    import workloads as W
+    for name in ("bruss3d", "diffreact2d", "bruss2d", "swe_box"):
+        full = bench.bench_config(name)
+        cfg, what = bench.cpu_sample_config(name)
+        assert (cfg["nx"], cfg["ny"], cfg["nz"], cfg["param"]) == \
+            (full["nx"], full["ny"], full["nz"], full["param"])
+        assert cfg["batch"] == 1 and cfg["N"] == min(16, full["N"])
+        dT = (full["tN"] - full["t0"]) / full["N"]
+        assert abs((cfg["tN"] - cfg["t0"]) / cfg["N"] - dT) < 1e-12 * dT
+        assert cfg["nG"] == full["nG"] and cfg["nF"] <= full["nF"]
+        assert cfg["N"] * W.dim(cfg) * cfg["nF"] <= max(2e9, cfg["N"] * W.dim(cfg) * 50)
+        assert name in what
 
 
 def test_reference_other_ranks_print_nothing(bench_mod, capsys, monkeypatch):
