@@ -1247,10 +1247,12 @@ __device__ __forceinline__ void mixed_body(const FusedParams& P) {
   // (stage 0's before the loop) and complete bytes on mbarrier s & 1, in
   // its phase of parity (s >> 1) & 1.  Thread 0 arms that phase one stage
   // ahead, at the start of stage s - 1 (the mbarrier's previous phase, stage
-  // s - 2, completed before stage s - 2 began), and the threads that read
-  // ghost rows (those owning an edge row) wait for it at the end of stage
-  // s - 1, with cluster-scope acquire, before the CTA barrier that closes
-  // the stage.  A CTA whose wait gave up therefore stops before computing
+  // s - 2, completed before stage s - 2 began), and thread 0 waits for it
+  // at the end of stage s - 1, with cluster-scope acquire, before the CTA
+  // barrier that closes the stage (the barrier then orders the ghost rows
+  // before every thread's reads of them: one cluster-scope acquire per CTA
+  // and stage instead of one per thread that owns an edge row).  A CTA
+  // whose wait gave up therefore stops before computing
   // stage s and pushes no further rows.  Since a CTA computes stage s only
   // after both neighbours' stage-s rows arrived, i.e. after both neighbours
   // computed stage s - 1, the stop stages of adjacent CTAs differ by at most
@@ -1260,7 +1262,8 @@ __device__ __forceinline__ void mixed_body(const FusedParams& P) {
     if (remote && s < nst && threadIdx.x == 0) mbar_expect(mb0 + 8u * (s & 1), tx_bytes);
   };
   auto wait_rows = [&](int s) {
-    if (remote && s < nst && edge && !halo_wait(mb0 + 8u * (s & 1), (uint32_t)((s >> 1) & 1))) {
+    if (remote && s < nst && threadIdx.x == 0 &&
+        !halo_wait(mb0 + 8u * (s & 1), (uint32_t)((s >> 1) & 1))) {
       abort_flag[s & 1] = 1;
       if (P.err) atomicExch(P.err, 1);
     }

@@ -66,13 +66,19 @@ def test_member_joining_mid_flight_equals_solving_alone(R, precision):
             assert errs[j] <= 2e-7 and abs(K - refs[j][1]) <= 1
 
 
-def test_server_stream_results_equal_their_solo_solves(R):
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_server_stream_results_equal_their_solo_solves(R, precision):
+    """Every request of a served stream (two grid classes, arrivals while
+    others run, two slots per pool) equals the same request solved alone:
+    bit for bit in FP64; in mixed precision within the FP32 stencil bound
+    (2e-7 relative) at the same K, or within the solve bound (1e-5) when
+    the iteration count differs by one."""
     from paper_2411_06225_gb300.serve import Server
     reqs = []
     for k, (g, N) in enumerate([(32, 8), (32, 8), (64, 8), (32, 8), (64, 8), (32, 16)]):
         cfg = W.config("swe2d", nx=g, ny=g, N=N, nF=0, nG=0, seed=100 + k, max_iters=8)
         reqs.append(cfg)
-    srv = Server(precision="fp64", slots=2, reserve_bytes=1 << 30)
+    srv = Server(precision=precision, slots=2, reserve_bytes=1 << 30)
     srv.start()
     futs = []
     for cfg in reqs:
@@ -82,6 +88,13 @@ def test_server_stream_results_equal_their_solo_solves(R):
     srv.stop()
     assert srv.turns > 0
     for cfg, res in zip(reqs, out):
-        ref, K = alone(R, dict(cfg, seed=srv.weight_seed), W.initial_condition(cfg)[0], "fp64")
-        assert res["converged"] and res["K"] == K
-        assert np.array_equal(res["U"], ref)
+        ref, K = alone(R, dict(cfg, seed=srv.weight_seed), W.initial_condition(cfg)[0],
+                       precision)
+        assert res["converged"]
+        if precision == "fp64":
+            assert res["K"] == K
+            assert np.array_equal(res["U"], ref)
+        else:
+            e = np.abs(res["U"] - ref).max() / np.abs(ref).max()
+            assert abs(res["K"] - K) <= 1
+            assert e <= (2e-7 if res["K"] == K else 1e-5), (res["K"], K, e)
