@@ -38,6 +38,7 @@ struct Geom {
   int outer;       // extent of the axis split across a cluster (x/y/z for 1/2/3D)
   long long plane; // cells per outer index
   int bc;          // rnp_bc: 0 periodic, 1 no-flux walls (wall neighbour = the cell)
+  bool iso;        // equal grid spacing on every axis the operator has
 };
 
 // PDE constants, precomputed on the host in FP64 exactly as the plain

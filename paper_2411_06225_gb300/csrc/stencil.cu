@@ -81,10 +81,18 @@ Geom make_geom(const rnp_problem& p) {
     default: g.kp = -1; g.ncomp = 1; g.dims = 1;
   }
   g.d = g.n * g.ncomp;
+  g.iso = false;
   if (g.dims == 1) { g.outer = 1; g.plane = p.nx; }
   else if (g.dims == 2) { g.outer = p.ny; g.plane = p.nx; }
   else { g.outer = p.nz; g.plane = (long long)p.nx * p.ny; }
   g.bc = p.bc;
+  // equal spacing on every axis of a reaction-diffusion operator (1/h^2
+  // compared exactly as the kernels receive it)
+  const Coef c = make_coef(p, g);
+  if (g.kp == KP_BRUSS2 || g.kp == KP_BRUSS3)
+    g.iso = c.k[5] == c.k[6] && (g.dims < 3 || c.k[6] == c.k[7]);
+  else if (g.kp == KP_DIFFREACT)
+    g.iso = c.k[3] == c.k[4];
   return g;
 }
 
@@ -100,10 +108,13 @@ Coef make_coef(const rnp_problem& p, const Geom& g) {
     case KP_HEAT1: case KP_HEAT2: case KP_HEAT3:
       c.k[0] = P[0]; c.k[1] = ix2; c.k[2] = iy2; c.k[3] = iz2; break;
     case KP_DIFFREACT:
-      c.k[0] = P[0]; c.k[1] = P[1]; c.k[2] = P[2]; c.k[3] = ix2; c.k[4] = iy2; break;
+      c.k[0] = P[0]; c.k[1] = P[1]; c.k[2] = P[2]; c.k[3] = ix2; c.k[4] = iy2;
+      // diffusion coefficients over h^2 (equal spacing; mixed kernel only)
+      c.k[5] = P[0] * ix2; c.k[6] = P[1] * ix2; break;
     case KP_BRUSS2: case KP_BRUSS3:
       c.k[0] = P[0]; c.k[1] = P[1]; c.k[2] = P[2]; c.k[3] = P[3];
-      c.k[4] = 1.0 + P[1]; c.k[5] = ix2; c.k[6] = iy2; c.k[7] = iz2; break;
+      c.k[4] = 1.0 + P[1]; c.k[5] = ix2; c.k[6] = iy2; c.k[7] = iz2;
+      c.k[8] = P[2] * ix2; c.k[9] = P[3] * ix2; break;
     case KP_SWE:
       c.k[0] = P[0]; c.k[1] = 0.5 * P[0]; c.k[2] = 1.0 / hx; c.k[3] = 1.0 / hy; break;
   }
@@ -201,11 +212,14 @@ static FusedFn mixed_fn_narrow(int kp, int PX, int RS, bool XS, bool WALL, bool 
 }
 
 // The mixed kernel for a block of `threads`: blocks above 512 threads run
-// the wide instantiation (80 registers per thread).
-static FusedFn mixed_fn(int kp, int PX, int RS, bool XS, bool WALL, bool RK, int threads) {
+// the wide instantiation (72 registers per thread, state in tensor memory,
+// equal grid spacing only).
+static FusedFn mixed_fn(const Geom& g, int PX, int RS, bool XS, bool WALL, bool RK,
+                        int threads) {
   if (threads > 512)
-    return threads <= kWideThreads ? mixed_wide_fn(kp, PX, RS, XS, WALL, RK) : nullptr;
-  return mixed_fn_narrow(kp, PX, RS, XS, WALL, RK);
+    return threads <= kWideThreads ? mixed_wide_fn(g.kp, PX, RS, XS, WALL, RK, g.iso)
+                                   : nullptr;
+  return mixed_fn_narrow(g.kp, PX, RS, XS, WALL, RK);
 }
 
 static const int kRs[] = {1, 2, 4, 8, 16};
@@ -217,15 +231,23 @@ static int round_R(long long cells_per_thread) {
   return -1;
 }
 
-static size_t smem_bytes(const Geom& g, bool fp32, int CS) {
+// Byte offset of the mixed kernel's mbarriers: the 16-byte aligned end of
+// its two stage buffers (with two ghost rows each) and, unless the low words
+// live in tensor memory (the wide kernel, tm), the low words.
+static size_t mixed_tail_offset(const Geom& g, int CS, bool tm) {
   const long long ncell = (long long)(g.outer / CS) * g.plane;
-  // FP64 kernel: two stage buffers; mixed kernel: two stage buffers with two
-  // ghost rows each, the low words, then two mbarriers, the 16-byte halo
-  // target table, two abort flags, the neighbours' two stop stages and the
-  // tensor-memory base (64 bytes)
+  const size_t f = (2 * (size_t)g.ncomp * (ncell + 2 * g.plane) +
+                    (tm ? 0 : (size_t)g.ncomp * ncell)) * 4;
+  return (f + 15) & ~(size_t)15;
+}
+
+static size_t smem_bytes(const Geom& g, bool fp32, int CS, bool tm = false) {
+  const long long ncell = (long long)(g.outer / CS) * g.plane;
+  // FP64 kernel: two stage buffers; mixed kernel: the buffers above, then
+  // two mbarriers, the 16-byte halo target table, two abort flags, the
+  // neighbours' two stop stages and the tensor-memory base (64 bytes)
   if (!fp32) return 2 * (size_t)g.ncomp * ncell * 8;
-  const size_t f = (2 * (size_t)g.ncomp * (ncell + 2 * g.plane) + (size_t)g.ncomp * ncell) * 4;
-  return ((f + 15) & ~(size_t)15) + 64;
+  return mixed_tail_offset(g, CS, tm) + 64;
 }
 
 // Why the configurations tried were not launchable (for error messages):
@@ -322,8 +344,8 @@ static bool try_cfg(const Geom& g, bool fp32, int CS, int threads, int nitems,
   if (g.dims == 1 && CS != 1) return false;
   const long long nloc = g.outer / CS;
   const long long ncell = nloc * g.plane;
-  const size_t smem = smem_bytes(g, fp32, CS);
-  if (fp32 && smem <= (size_t)kMaxSmem) {
+  const size_t smem_n = smem_bytes(g, fp32, CS), smem_t = smem_bytes(g, fp32, CS, true);
+  if (fp32 && smem_t <= (size_t)kMaxSmem) {
     // mixed kernel: PX x-points by RS rows per thread; the most threads
     // (up to 512) whose register tile fits, or exactly `threads` if given
     const int pxs[] = {2, 4};
@@ -343,14 +365,16 @@ static bool try_cfg(const Geom& g, bool fp32, int CS, int threads, int nitems,
         const long long t = tiles * (nloc / RS);
         if (t > kWideThreads || t < 1) continue;
         // the wide kernel's tensor-memory accesses are warp-collective: whole
-        // warps only
+        // warps only; its low words live in tensor memory
         if (t > 512 && t % 32) continue;
+        const size_t smem = t > 512 ? smem_t : smem_n;
+        if (smem > (size_t)kMaxSmem) continue;
         if (threads > 0 && t != threads) continue;
         // the RK4 and the Euler instantiation of this tile (the RK4 one is
         // the larger: it decides launchability); blocks above 512 threads
         // exist only as the wide kernel's tiles
-        FusedFn fn = mixed_fn(g.kp, PX, RS, x_shuffles(g, PX), g.bc != 0, true, (int)t);
-        FusedFn fe = mixed_fn(g.kp, PX, RS, x_shuffles(g, PX), g.bc != 0, false, (int)t);
+        FusedFn fn = mixed_fn(g, PX, RS, x_shuffles(g, PX), g.bc != 0, true, (int)t);
+        FusedFn fe = mixed_fn(g, PX, RS, x_shuffles(g, PX), g.bc != 0, false, (int)t);
         if (!fn || !fe || !launchable(fn, CS, (int)t, smem, nitems) ||
             !launchable(fe, CS, (int)t, smem, nitems))
           continue;
@@ -523,7 +547,7 @@ cudaError_t launch_stencil_fused(const Geom& g, const Coef& c, bool fp32, int sc
   // a mixed-precision context uses the FP64 kernel where no FP32 tile fits
   const bool use_mixed = fp32 && cfg.px > 0;
   if (scheme == SCHEME_RK8 && use_mixed) return cudaErrorInvalidValue;  // FP64 only
-  FusedFn fn = use_mixed ? mixed_fn(g.kp, cfg.px, cfg.rs, x_shuffles(g, cfg.px), g.bc != 0,
+  FusedFn fn = use_mixed ? mixed_fn(g, cfg.px, cfg.rs, x_shuffles(g, cfg.px), g.bc != 0,
                                     scheme == SCHEME_RK4, cfg.threads)
                : scheme == SCHEME_RK8 ? fused_rk8_fn(g.kp, cfg.R)
                                       : fused_fn(g.kp, cfg.R);
@@ -542,15 +566,15 @@ cudaError_t launch_stencil_fused(const Geom& g, const Coef& c, bool fp32, int sc
   P.nloc = g.outer / cfg.cluster;
   P.mcell = (P.nloc + 2) * (int)g.plane;
   P.mcl = P.nloc * (int)g.plane;
-  P.moff = (int)((((size_t)2 * g.ncomp * P.mcell + (size_t)g.ncomp * P.mcl) * 4 + 15) &
-                 ~(size_t)15);
+  const bool tm = use_mixed && cfg.threads > 512;
+  P.moff = use_mixed ? (int)mixed_tail_offset(g, cfg.cluster, tm) : 0;
   if (scheme == SCHEME_RK8) rk8_tableau(P.rk);
   else memset(P.rk, 0, sizeof(P.rk));
   cudaLaunchConfig_t lc = {};
   cudaLaunchAttribute at[1];
   lc.gridDim = dim3(cfg.cluster * it.n);
   lc.blockDim = dim3(cfg.threads);
-  lc.dynamicSmemBytes = smem_bytes(g, use_mixed, cfg.cluster);
+  lc.dynamicSmemBytes = smem_bytes(g, use_mixed, cfg.cluster, tm);
   lc.stream = st;
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = cfg.cluster;

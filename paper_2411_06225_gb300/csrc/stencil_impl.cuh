@@ -823,13 +823,13 @@ __device__ __forceinline__ void tm_wait_st() {
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
-template <int KP, int PX, int RS, int STAGE, bool XS, bool WALL, bool TM>
+template <int KP, int PX, int RS, int STAGE, bool XS, bool WALL, bool TM, bool ISO>
 __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* __restrict__ B,
                                             float* __restrict__ Bn, float* ulo,
                                             float (&uh)[RS][KT<KP>::NC][PX],
                                             float (&acc)[RS][KT<KP>::NC][PX], uint32_t tm,
                                             int ncell, int plane, int nloc, int ofirst, int dir,
-                                            int rowoff, int woff, int eoff, int yn_off, int ys_off,
+                                            int rowoff, int dW, int dE, int dN, int dS,
                                             bool euler, const HaloOut& ho, unsigned xmask,
                                             int xw, int xwest, int xeast, bool xlo, bool xhi,
                                             const float* __restrict__ bth) {
@@ -842,6 +842,10 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
   constexpr bool kPacked =
       PX % 2 == 0 && (KP == KP_DIFFREACT || KP == KP_BRUSS2 || KP == KP_BRUSS3);
   constexpr int kLx = KP == KP_DIFFREACT ? 3 : 5;
+  // ISO (equal spacing h on every axis): the Laplacian is the neighbour sum
+  // minus 2 DIMS times the centre, and the diffusion coefficients come
+  // premultiplied by 1/h^2: kk[kIsoD], kk[kIsoD + 1] = D_u / h^2, D_v / h^2
+  constexpr int kIsoD = KP == KP_DIFFREACT ? 5 : 8;
   // Only the shallow-water fluxes tell the two outer neighbours apart; the
   // other right-hand sides take their sum.
   constexpr bool kOrdered = KP == KP_SWE;
@@ -850,27 +854,39 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
   // the one being updated, `ahead` the row in front of it (ghost rows -1
   // and nloc hold the neighbours' edge rows)
   float back[NC][PX], cur[NC][PX], ahead[NC][PX];
+  // this row's first cell in the read buffer, the write buffer, the low
+  // words and the bottom factors (species 0); advanced by rstep per row.
+  // The neighbours sit at fixed offsets from it: dW / dE the first cells of
+  // the west / east tiles, dN / dS the y neighbours (3D), rstep the next row.
+  const int c0 = ofirst * plane + rowoff;
+  const float* pB = B + c0;
+  float* pBn = Bn + c0;
+  float* pL = TM ? nullptr : ulo + c0;
+  const float* pT = bth ? bth + c0 : nullptr;
 #pragma unroll
   for (int q = 0; q < NC; ++q) {
-    const float* row = B + q * ncell + ofirst * plane + rowoff;
-    ld_vec<PX>(row, cur[q]);
-    if (DIMS >= 2) ld_vec<PX>(row - rstep, back[q]);
+    ld_vec<PX>(pB + q * ncell, cur[q]);
+    if (DIMS >= 2) ld_vec<PX>(pB + q * ncell - rstep, back[q]);
   }
   // (TM: the rows' state is addressed in tensor memory, so the row loop can
   // stay rolled, which keeps one row's values live at a time)
 #pragma unroll (TM ? 1 : RS)
   for (int r = 0; r < RS; ++r) {
-    const int o = ofirst + dir * r;
-    const int cb = o * plane + rowoff;    // first cell of this tile row
     // this row's step state and accumulator: the register tile's row, or
     // (TM) a copy loaded from tensor memory (columns r NC PX .. of the
     // thread's uh block, then of its accumulator block RS NC PX further)
-    float ur[NC][PX], ar[NC][PX];
+    // (TM: the low words of the compensated state too, at 2 RS NC PX, read
+    // and written in Euler steps and the last RK stage)
+    float ur[NC][PX], ar[NC][PX], lr[NC][PX];
     if constexpr (TM) {
       tm_ld<NC * PX>(tm + (uint32_t)(r * NC * PX), &ur[0][0]);
       if (!euler && STAGE > 0) {
         tm_ld<NC * PX>(tm + (uint32_t)((RS + r) * NC * PX), &ar[0][0]);
         tm_wait_ld<NC * PX>(&ar[0][0]);
+      }
+      if (euler || STAGE == 3) {
+        tm_ld<NC * PX>(tm + (uint32_t)((2 * RS + r) * NC * PX), &lr[0][0]);
+        tm_wait_ld<NC * PX>(&lr[0][0]);
       }
       tm_wait_ld<NC * PX>(&ur[0][0]);
     }
@@ -878,12 +894,12 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
     float (&A_)[NC][PX] = TM ? ar : acc[r];
 #pragma unroll
     for (int q = 0; q < NC; ++q)
-      if (DIMS >= 2) ld_vec<PX>(B + q * ncell + cb + rstep, ahead[q]);
+      if (DIMS >= 2) ld_vec<PX>(pB + q * ncell + rstep, ahead[q]);
     float ew[NC], ee[NC];
     float yn[NC][PX], ys[NC][PX];
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
-      const float* Bq = B + q * ncell + o * plane;
+      const float* Bq = pB + q * ncell;   // this tile's first cell, species q
       if constexpr (XS) {
         // x neighbours from the adjacent lanes: an x-row spans xw lanes, so
         // a width-xw shuffle wraps periodically in x
@@ -892,14 +908,22 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
       } else if constexpr (kPacked) {
         // x neighbours: the adjacent tiles' edge values, loaded as scalars
         // into one register pair for the packed arithmetic
-        ew[q] = Bq[woff + PX - 1];
-        ee[q] = Bq[eoff];
+        if constexpr (PX == 4) {
+          // the last pair of the west tile and the first pair of the east
+          // tile: 8-byte loads halve the bank conflicts of the strided
+          // 4-byte loads
+          ew[q] = reinterpret_cast<const float2*>(Bq + dW + PX - 2)->y;
+          ee[q] = reinterpret_cast<const float2*>(Bq + dE)->x;
+        } else {
+          ew[q] = Bq[dW + PX - 1];
+          ee[q] = Bq[dE];
+        }
       } else {
         // x neighbours: aligned vector loads of the adjacent tiles (lanes
         // read consecutive vectors, so there is no bank conflict); keep the edge
         float vw[PX], ve[PX];
-        ld_vec<PX>(Bq + woff, vw);
-        ld_vec<PX>(Bq + eoff, ve);
+        ld_vec<PX>(Bq + dW, vw);
+        ld_vec<PX>(Bq + dE, ve);
         ew[q] = vw[PX - 1];
         ee[q] = ve[0];
       }
@@ -911,16 +935,16 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
         if (xhi) ee[q] = (kFlip && q == 1) ? -cur[q][PX - 1] : cur[q][PX - 1];
       }
       if (DIMS == 3) {
-        ld_vec<PX>(Bq + yn_off, yn[q]);
-        ld_vec<PX>(Bq + ys_off, ys[q]);
+        ld_vec<PX>(Bq + dN, yn[q]);
+        ld_vec<PX>(Bq + dS, ys[q]);
       }
     }
     // shallow water: the bottom term's per-cell factors of this tile row
     float bx[PX], by[PX];
     if constexpr (KP == KP_SWE) {
       if (bth) {
-        ld_vec<PX>(bth + cb, bx);
-        ld_vec<PX>(bth + P.n + cb, by);
+        ld_vec<PX>(pT, bx);
+        ld_vec<PX>(pT + P.n, by);
       }
     }
     float wout[NC][PX];
@@ -943,7 +967,13 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
           const float2 hi = pk(ahead[q][p0], ahead[q][p1]);
           const float2 lo = pk(back[q][p0], back[q][p1]);
           float2 l;
-          if constexpr (DIMS == 2) {
+          if constexpr (ISO) {
+            // unscaled: (sum of the 2 DIMS neighbours) - 2 DIMS C
+            float2 sum = add2(EW, add2(hi, lo));
+            if constexpr (DIMS == 3)
+              sum = add2(sum, add2(pk(yn[q][p0], yn[q][p1]), pk(ys[q][p0], ys[q][p1])));
+            l = fma2(pk1(-2.f * DIMS), C, sum);
+          } else if constexpr (DIMS == 2) {
             const float2 lx = mul2(fma2(pk1(-2.f), C, EW), pk1(kk[kLx]));
             l = fma2(fma2(pk1(-2.f), C, add2(hi, lo)), pk1(kk[kLx + 1]), lx);
           } else {
@@ -959,22 +989,24 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
         if constexpr (KP == KP_DIFFREACT) {
           // Du lap u + (u - u^3 - c - v);  Dv lap v + (u - v)
           const float2 a3 = mul2(mul2(a, a), a);
-          kq[0] = fma2(pk1(kk[0]), lq[0], sub2(sub2(sub2(a, a3), pk1(kk[2])), b));
-          kq[1] = fma2(pk1(kk[1]), lq[1], sub2(a, b));
+          constexpr int iD = ISO ? kIsoD : 0;
+          kq[0] = fma2(pk1(kk[iD]), lq[0], sub2(sub2(sub2(a, a3), pk1(kk[2])), b));
+          kq[1] = fma2(pk1(kk[iD + 1]), lq[1], sub2(a, b));
         } else {
           // D0 lap u + (a - (1 + b) u + v u^2);  D1 lap v + (b u - v u^2)
+          constexpr int iD = ISO ? kIsoD : 2;
           const float2 ba2 = mul2(b, mul2(a, a));
-          kq[0] = fma2(pk1(kk[2]), lq[0], add2(fma2(pk1(-kk[4]), a, pk1(kk[0])), ba2));
-          kq[1] = fma2(pk1(kk[3]), lq[1], fma2(pk1(kk[1]), a, mul2(pk1(-1.f), ba2)));
+          kq[0] = fma2(pk1(kk[iD]), lq[0], add2(fma2(pk1(-kk[4]), a, pk1(kk[0])), ba2));
+          kq[1] = fma2(pk1(kk[iD + 1]), lq[1], fma2(pk1(kk[1]), a, mul2(pk1(-1.f), ba2)));
         }
 #pragma unroll
         for (int q = 0; q < NC; ++q) {
           float2 U = pk(U_[q][p0], U_[q][p1]);
           float2 w;
           if (euler) {
-            float2 l = *reinterpret_cast<const float2*>(ulo + q * ncl + cb + p0);
+            float2 l = TM ? pk(lr[q][p0], lr[q][p1]) : *reinterpret_cast<const float2*>(pL + q * ncl + p0);
             two_sum_acc2(U, l, mul2(pk1(dt), kq[q]));
-            *reinterpret_cast<float2*>(ulo + q * ncl + cb + p0) = l;
+            if constexpr (TM) { lr[q][p0] = l.x; lr[q][p1] = l.y; } else *reinterpret_cast<float2*>(pL + q * ncl + p0) = l;
             w = U;
           } else if (STAGE == 0) {
             A_[q][p0] = kq[q].x; A_[q][p1] = kq[q].y;
@@ -985,9 +1017,9 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
             w = fma2(pk1(STAGE == 1 ? h2 : dt), kq[q], U);
           } else {
             const float2 A2 = add2(pk(A_[q][p0], A_[q][p1]), kq[q]);
-            float2 l = *reinterpret_cast<const float2*>(ulo + q * ncl + cb + p0);
+            float2 l = TM ? pk(lr[q][p0], lr[q][p1]) : *reinterpret_cast<const float2*>(pL + q * ncl + p0);
             two_sum_acc2(U, l, mul2(pk1(h6), A2));
-            *reinterpret_cast<float2*>(ulo + q * ncl + cb + p0) = l;
+            if constexpr (TM) { lr[q][p0] = l.x; lr[q][p1] = l.y; } else *reinterpret_cast<float2*>(pL + q * ncl + p0) = l;
             w = U;
           }
           U_[q][p0] = U.x; U_[q][p1] = U.y;
@@ -1021,9 +1053,9 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
         for (int q = 0; q < NC; ++q) {
           float w;
           if (euler) {
-            float l = ulo[q * ncl + cb + p];
+            float l = TM ? lr[q][p] : pL[q * ncl + p];
             two_sum_acc(U_[q][p], l, __fmul_rn(dt, k[q]));
-            ulo[q * ncl + cb + p] = l;
+            if constexpr (TM) lr[q][p] = l; else pL[q * ncl + p] = l;
             w = U_[q][p];
           } else if (STAGE == 0) {
             A_[q][p] = k[q];
@@ -1036,9 +1068,9 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
             w = U_[q][p] + dt * k[q];
           } else {
             const float a = A_[q][p] + k[q];
-            float l = ulo[q * ncl + cb + p];
+            float l = TM ? lr[q][p] : pL[q * ncl + p];
             two_sum_acc(U_[q][p], l, __fmul_rn(h6, a));
-            ulo[q * ncl + cb + p] = l;
+            if constexpr (TM) lr[q][p] = l; else pL[q * ncl + p] = l;
             w = U_[q][p];
           }
           wout[q][p] = w;
@@ -1048,12 +1080,16 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
     if constexpr (TM) {
       // the state changes in Euler steps and the last RK stage, the
       // accumulator in the first three RK stages
-      if (euler || STAGE == 3) tm_st<NC * PX>(tm + (uint32_t)(r * NC * PX), &ur[0][0]);
-      else tm_st<NC * PX>(tm + (uint32_t)((RS + r) * NC * PX), &ar[0][0]);
+      if (euler || STAGE == 3) {
+        tm_st<NC * PX>(tm + (uint32_t)(r * NC * PX), &ur[0][0]);
+        tm_st<NC * PX>(tm + (uint32_t)((2 * RS + r) * NC * PX), &lr[0][0]);
+      } else {
+        tm_st<NC * PX>(tm + (uint32_t)((RS + r) * NC * PX), &ar[0][0]);
+      }
     }
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
-      st_vec<PX>(Bn + q * ncell + cb, wout[q]);
+      st_vec<PX>(pBn + q * ncell, wout[q]);
       if (DIMS >= 2) {
         // edge rows are visited first: row 0 (walking up) or nloc - 1 (down);
         // a CTA with a single row group also sends its last row at r = RS - 1
@@ -1065,6 +1101,10 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
         for (int p = 0; p < PX; ++p) { back[q][p] = cur[q][p]; cur[q][p] = ahead[q][p]; }
       }
     }
+    pB += rstep;
+    pBn += rstep;
+    if constexpr (!TM) pL += rstep;
+    if (pT) pT += rstep;
   }
   if constexpr (TM) tm_wait_st();
 }
@@ -1075,7 +1115,7 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
 // 128 registers each) and k_stencil_mixed_wide (up to 800 threads capped at
 // 80 registers, for slices whose CTA share leaves one CTA per SM: there the
 // wider block holds twice the warps and a smaller register tile per thread).
-template <int KP, int PX, int RS, bool XS, bool WALL, bool RK, bool TM>
+template <int KP, int PX, int RS, bool XS, bool WALL, bool RK, bool TM, bool ISO>
 __device__ __forceinline__ void mixed_body(const FusedParams& P) {
   constexpr int NC = KT<KP>::NC, DIMS = KT<KP>::DIMS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1093,7 +1133,8 @@ __device__ __forceinline__ void mixed_body(const FusedParams& P) {
   const int ncl = P.mcl;       // nloc * plane
   float* const buf0 = reinterpret_cast<float*>(smem_raw) + plane;   // row 0 of buffer 0
   float* const buf1 = buf0 + NC * ncell;
-  float* const ulo = reinterpret_cast<float*>(smem_raw) + 2 * NC * ncell;
+  // the low words (not with TM: they live in tensor memory)
+  float* const ulo = TM ? nullptr : reinterpret_cast<float*>(smem_raw) + 2 * NC * ncell;
   // (P.moff = the 16-byte aligned end of the buffers: 4 (2 NC ncell + NC ncl);
   // after it 64 bytes: mbarriers, target table, flags, stop stages, TMEM base)
   uint64_t* const mbar = reinterpret_cast<uint64_t*>(smem_raw + P.moff);
@@ -1117,11 +1158,12 @@ __device__ __forceinline__ void mixed_body(const FusedParams& P) {
   // y neighbours inside a 3D plane: periodic, or the row itself at a wall
   const int yn_row = yrow + 1 == ny ? (WALL ? yrow : 0) : yrow + 1;
   const int ys_row = yrow == 0 ? (WALL ? 0 : ny - 1) : yrow - 1;
-  const int yn_off = (DIMS == 3 ? yn_row * nx : 0) + x0;
-  const int ys_off = (DIMS == 3 ? ys_row * nx : 0) + x0;
+  // offsets of the y neighbours from the tile's first cell (3D)
+  const int dN = DIMS == 3 ? (yn_row - yrow) * nx : 0;
+  const int dS = DIMS == 3 ? (ys_row - yrow) * nx : 0;
   // first cells of the tiles west and east of this one (periodic in x; at a
   // wall the value is replaced by the cell's own)
-  const int woff = yrow * nx + (xw + 1 - PX), eoff = yrow * nx + xe;
+  const int dW = (xw + 1 - PX) - x0, dE = xe - x0;
   const bool xlo = WALL && x0 == 0, xhi = WALL && x0 + PX == nx;
   const bool first = o0 == 0, last = o0 + RS == nloc;
   const bool edge = DIMS >= 2 && (first || last);
@@ -1194,15 +1236,17 @@ __device__ __forceinline__ void mixed_body(const FusedParams& P) {
         uh[r][q][p] = h;
         acc[r][q][p] = 0.f;
         buf0[q * ncell + o * plane + rowoff + p] = h;
-        ulo[q * ncl + o * plane + rowoff + p] = (float)(v - (double)h);
+        if constexpr (TM) acc[r][q][p] = (float)(v - (double)h);   // staged for TMEM
+        else ulo[q * ncl + o * plane + rowoff + p] = (float)(v - (double)h);
       }
-  // TM: 256 TMEM columns for the CTA (at most 8 warps share a lane
-  // quadrant, each using 2 RS NC PX <= 32 columns), allocated by warp 0;
-  // the allocation writes the base address to tm_base
+  // TM: 512 TMEM columns for the CTA (at most 8 warps share a lane
+  // quadrant, each using 3 RS NC PX <= 48 columns: step state, accumulator,
+  // low words), allocated by warp 0; the allocation writes the base address
+  // to tm_base
   volatile uint32_t* const tm_base = reinterpret_cast<volatile uint32_t*>(stop_in + 2);
   if constexpr (TM) {
     if (threadIdx.x < 32) {
-      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
                        cta_smem_u32(const_cast<uint32_t*>(tm_base)))
                    : "memory");
       asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -1218,9 +1262,12 @@ __device__ __forceinline__ void mixed_body(const FusedParams& P) {
   if constexpr (TM) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t w = threadIdx.x >> 5;
-    tm = *tm_base + ((32u * (w & 3u)) << 16) + (w >> 2) * (uint32_t)(2 * RS * NC * PX);
+    tm = *tm_base + ((32u * (w & 3u)) << 16) + (w >> 2) * (uint32_t)(3 * RS * NC * PX);
 #pragma unroll
-    for (int r = 0; r < RS; ++r) tm_st<NC * PX>(tm + (uint32_t)(r * NC * PX), &uh[r][0][0]);
+    for (int r = 0; r < RS; ++r) {
+      tm_st<NC * PX>(tm + (uint32_t)(r * NC * PX), &uh[r][0][0]);
+      tm_st<NC * PX>(tm + (uint32_t)((2 * RS + r) * NC * PX), &acc[r][0][0]);  // low words
+    }
     tm_wait_st();
   }
   // stage 0's halo: the initial edge rows
@@ -1278,8 +1325,9 @@ __device__ __forceinline__ void mixed_body(const FusedParams& P) {
     return abort_flag[s & 1] != 0;
   };
 #define RNP_MIXED_STAGE(STG, BIN, BOUT, PAR, ON, EUL)                                          \
-  mixed_stage<KP, PX, RS, STG, XS, WALL, TM>(P, BIN, BOUT, ulo, uh, acc, tm, ncell, plane, nloc, \
-                                         ofirst, dir, rowoff, woff, eoff, yn_off, ys_off,    \
+  mixed_stage<KP, PX, RS, STG, XS, WALL, TM, ISO>(P, BIN, BOUT, ulo, uh, acc, tm, ncell, plane, \
+                                                  nloc,                                       \
+                                         ofirst, dir, rowoff, dW, dE, dN, dS,                \
                                          EUL, halo_out((PAR) ^ 1, ON), xmask, xsw, xwest,    \
                                          xeast, xlo, xhi, bth)
 
@@ -1372,13 +1420,15 @@ __device__ __forceinline__ void mixed_body(const FusedParams& P) {
 #pragma unroll
     for (int r = 0; r < RS; ++r) {
       tm_ld<NC * PX>(tm + (uint32_t)(r * NC * PX), &uh[r][0][0]);
+      tm_ld<NC * PX>(tm + (uint32_t)((2 * RS + r) * NC * PX), &acc[r][0][0]);  // low words
       tm_wait_ld<NC * PX>(&uh[r][0][0]);
+      tm_wait_ld<NC * PX>(&acc[r][0][0]);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (threadIdx.x < 32)
-      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(*tm_base)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(*tm_base)
                    : "memory");
   }
   double* out = P.out + item_off(P.it.dst_off, P.it.dst_base, P.it.dst_stride, item) + base;
@@ -1391,7 +1441,8 @@ __device__ __forceinline__ void mixed_body(const FusedParams& P) {
 #pragma unroll
       for (int p = 0; p < PX; ++p) {
         const int o = ofirst + dir * r;
-        const double v = (double)uh[r][q][p] + (double)ulo[q * ncl + o * plane + rowoff + p];
+        const double v = (double)uh[r][q][p] +
+                         (double)(TM ? acc[r][q][p] : ulo[q * ncl + o * plane + rowoff + p]);
         out[q * P.n + o * plane + rowoff + p] = v;
         if (out2) out2[q * P.n + o * plane + rowoff + p] = v;
       }
@@ -1399,7 +1450,7 @@ __device__ __forceinline__ void mixed_body(const FusedParams& P) {
 
 template <int KP, int PX, int RS, bool XS, bool WALL, bool RK>
 __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant__ FusedParams P) {
-  mixed_body<KP, PX, RS, XS, WALL, RK, false>(P);
+  mixed_body<KP, PX, RS, XS, WALL, RK, false, false>(P);
 }
 
 // Registers per thread of the wide kernel.  The register file is split
@@ -1410,10 +1461,12 @@ static constexpr int kWideRegs = 72;
 static constexpr int kWideThreads = 800;
 
 // The wide kernel keeps the step state and the accumulator in tensor memory
-// (TM), which leaves the registers to the stencil's working rows.
+// (TM), which leaves the registers to the stencil's working rows, and
+// requires equal grid spacing on every axis (ISO: a cheaper Laplacian with
+// fewer constants); the host falls back to the other kernel otherwise.
 template <int KP, int PX, int RS, bool XS, bool WALL, bool RK>
 __global__ void __maxnreg__(kWideRegs) k_stencil_mixed_wide(const __grid_constant__ FusedParams P) {
-  mixed_body<KP, PX, RS, XS, WALL, RK, true>(P);
+  mixed_body<KP, PX, RS, XS, WALL, RK, true, true>(P);
 }
 
 typedef void (*FusedFn)(const FusedParams);
@@ -1481,21 +1534,24 @@ inline FusedFn mixed_for(int PX, int RS, bool XS, bool WALL, bool RK) {
   return nullptr;
 }
 
-// The wide kernel's instantiations: tiles of at most 16 state values per
-// thread, periodic, x neighbours from shared memory (the configurations a
-// wide block is picked for: a slice whose CTA share fills the shared memory).
+// The wide kernel's instantiations: tiles of at most 20 state values per
+// thread (3 x 20 TMEM columns per warp, at most 7 warps per lane quadrant:
+// 420 of the 512 columns), periodic, x neighbours from shared memory (the
+// configurations a wide block is picked for: a slice whose CTA share fills
+// the shared memory).
 template <int KP, bool RK>
 inline FusedFn mixed_wide_for(int PX, int RS) {
   if (PX == 2 && RS == 1) return k_stencil_mixed_wide<KP, 2, 1, false, false, RK>;
   if (PX == 2 && RS == 2) return k_stencil_mixed_wide<KP, 2, 2, false, false, RK>;
   if (PX == 2 && RS == 4) return k_stencil_mixed_wide<KP, 2, 4, false, false, RK>;
+  if (PX == 2 && RS == 5) return k_stencil_mixed_wide<KP, 2, 5, false, false, RK>;
   if (PX == 4 && RS == 1) return k_stencil_mixed_wide<KP, 4, 1, false, false, RK>;
   if (PX == 4 && RS == 2) return k_stencil_mixed_wide<KP, 4, 2, false, false, RK>;
   return nullptr;
 }
-// defined in stencil_wide.cu: the 3D Brusselator's wide kernels (nullptr
-// for other operators and tiles)
-FusedFn mixed_wide_fn(int kp, int PX, int RS, bool XS, bool WALL, bool RK);
+// defined in stencil_wide.cu: the 3D Brusselator's wide kernels on grids of
+// equal spacing (nullptr for other operators, tiles and grids)
+FusedFn mixed_wide_fn(int kp, int PX, int RS, bool XS, bool WALL, bool RK, bool iso);
 
 // Per-PDE entry points, defined in stencil_<pde>.cu.
 #define RNP_STENCIL_DECL(NAME)                 \

@@ -5,8 +5,8 @@
 
 namespace rnp {
 
-FusedFn mixed_wide_fn(int kp, int PX, int RS, bool XS, bool WALL, bool RK) {
-  if (XS || WALL) return nullptr;
+FusedFn mixed_wide_fn(int kp, int PX, int RS, bool XS, bool WALL, bool RK, bool iso) {
+  if (XS || WALL || !iso) return nullptr;
   switch (kp) {
     case KP_BRUSS3: return RK ? mixed_wide_for<KP_BRUSS3, true>(PX, RS)
                               : mixed_wide_for<KP_BRUSS3, false>(PX, RS);
