@@ -13,11 +13,14 @@ seeded initial conditions (steady state plus U(0, 0.1) noise) solved
 together, M = 100 ReLU features, m = 4 neighbours, lambda = 1e-7,
 tol = 1e-6; the dataset arena is sized for 16 iterations.  The timed form is
 the mixed-precision fused path: FP32 stencils on a compensated (two-word)
-state, FP32 random features and neighbour distances on the CUDA cores, FP64
-ridge solve, correction and norm.  The 2D diffusion-reaction workload
-(128^2 x 2, N = 64, F = RK4 x 2000, G = Euler x 8) is measured after it and
-reported under "workloads", with the plain FP64 GPU form, the fused FP64
-form, BF16 tensor-core features and classic Parareal beside it.
+state, random features from BF16 operands with FP32 accumulation (the
+batched dataset rows of each iteration on the tcgen05 tensor cores, the
+sweep's single queries on CUDA cores), FP32 neighbour distances, FP64 ridge
+solve, correction and norm.  The 2D diffusion-reaction workload (128^2 x 2,
+N = 64, F = RK4 x 2000, G = Euler x 8) is measured after it and reported
+under "workloads", in its own timed form (FP32 features on CUDA cores: BF16
+features cost it one more iteration), with the plain FP64 GPU form, the
+fused FP64 form, BF16 features and classic Parareal beside it.
 
 value = fine cell-updates per second over the whole job (sum over ranks of
 the fine RK4 unknown-steps the solves performed / max over ranks of the
@@ -60,6 +63,11 @@ SECONDARY = ("diffreact2d",)
 METRIC = ("Parareal time-to-solution @tol 1e-6 vs plain FP64; cell-updates/s, %HBM; "
           "p50/p99")
 UNIT = "cell-updates/s"
+
+# Timed form per workload: BF16 random features where they leave the
+# iteration count unchanged and save time (3D Brusselator: K = 3 either way),
+# FP32 features elsewhere (diffusion-reaction: K = 5 with BF16, 4 without).
+TIMED_PRECISION = {"bruss3d": "mixed_bf16"}
 
 # Workload settings of the benchmark beyond the canonical configurations:
 # the 3D Brusselator's dataset arena is sized for 16 iterations (8 members x
@@ -262,12 +270,16 @@ def cpu_baseline(name: str | None = None) -> dict:
                       f"over {cores} threads"}
 
 
+def timed_precision(name: str, requested: str | None) -> str:
+    return requested or TIMED_PRECISION.get(name, "mixed")
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
     name = getattr(args, "workload", None) or WORKLOAD
-    precision = getattr(args, "precision", None) or "mixed"
+    precision = timed_precision(name, getattr(args, "precision", None))
     samples = []
     base = None
     for i in range(args.warmup + args.steps):
@@ -338,14 +350,15 @@ def measure(rnp, torch, name, args, rank, ws, dist, dev, stream, flush, headline
     B = cfg.get("batch", 1)
     u0_h = torch.as_tensor(W.initial_condition(cfg)).pin_memory()
     u0 = u0_h.to(dev)
+    prec = timed_precision(name, args.precision)
     if args.tile and headline:
         # a fixed stencil tiling (cluster, threads), e.g. to profile one
         # configuration: the autotuner's pick can differ under a profiler
         c_, t_ = (int(x) for x in args.tile.split(","))
-        prob = rnp.problem(cfg, precision=args.precision, exec="fused", autotune=0,
+        prob = rnp.problem(cfg, precision=prec, exec="fused", autotune=0,
                            cluster=c_, threads=t_)
     else:
-        prob = rnp.problem(cfg, precision=args.precision, exec="fused", autotune=1)
+        prob = rnp.problem(cfg, precision=prec, exec="fused", autotune=1)
     solver = rnp.Solver(prob, stream=stream)
     tiling = {"fine": solver.stencil_config("fine"), "coarse": solver.stencil_config("coarse")}
     steps = args.steps if headline else max(3, min(args.steps, 5))
@@ -428,14 +441,15 @@ def measure(rnp, torch, name, args, rank, ws, dist, dev, stream, flush, headline
                 "h2d_bytes_per_step": int(u0_h.numel() * 8),
                 "d2h_bytes_per_step": int(U_h.numel() * 8),
                 "ms_per_step": statistics.median(e2e_t) * 1e3},
-        "gpu_launches": launches, "wall_s": t_wall, "steps": steps,
+        "gpu_launches": launches, "wall_s": t_wall, "steps": steps, "precision": prec,
     }
     if clk is not None:
         res["clocks"] = clk
     return res, solver, u0, U, cfg
 
 
-def compare_forms(rnp, torch, name, cfg, args, stream, dev, u0, U, forms, parareal=True):
+def compare_forms(rnp, torch, name, cfg, args, stream, dev, u0, U, forms, parareal=True,
+                  timed="mixed"):
     """One solve of each other form of the workload on the same input."""
     extra = {}
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -455,22 +469,22 @@ def compare_forms(rnp, torch, name, cfg, args, stream, dev, u0, U, forms, parare
             extra[f"K_{label}"] = st2["K"]
             if label == "fp64_fused":
                 Uf = U2.clone()
-                extra["mixed_vs_fp64_max_abs"] = float((U - U2).abs().max().item())
-                extra["mixed_vs_fp64_rel"] = float(((U - U2).abs().max() /
+                extra["timed_vs_fp64_max_abs"] = float((U - U2).abs().max().item())
+                extra["timed_vs_fp64_rel"] = float(((U - U2).abs().max() /
                                                     U2.abs().max()).item())
             if label == "mixed_bf16" and Uf is not None:
                 extra["mixed_bf16_vs_fp64_rel"] = float(((U2 - Uf).abs().max() /
                                                          Uf.abs().max()).item())
-            if label == "mixed_bf16":
-                extra["mixed_bf16_vs_mixed_rel"] = float(((U2 - U).abs().max() /
-                                                          U.abs().max()).item())
+            if label in ("mixed_bf16", "mixed") and label != timed:
+                extra[f"{label}_vs_timed_rel"] = float(((U2 - U).abs().max() /
+                                                        U.abs().max()).item())
             del U2
     # classic Parareal (the correction of Eq. 4), same workload and mixed
     # precision: the in-repo counterpart of the paper's speed-up over Parareal
     if not parareal:
         return extra
     try:
-        with rnp.Solver(rnp.problem(cfg, precision=args.precision, exec="fused",
+        with rnp.Solver(rnp.problem(cfg, precision=timed, exec="fused",
                                     autotune=1, corr="parareal"), stream=stream) as s2:
             s2.solve(u0, check=False)          # warm-up (graph capture)
             torch.cuda.synchronize(dev)
@@ -536,12 +550,13 @@ def run_gpu(args):
             over.update(N=args.slices, tN=full["t0"] + args.slices * dT,
                         max_iters=min(args.slices, full["max_iters"]))
         cfg = bench_config(WORKLOAD, **over)
+        prec = timed_precision(WORKLOAD, args.precision)
         if args.tile:
             c_, t_ = (int(x) for x in args.tile.split(","))
-            prob = rnp.problem(cfg, precision=args.precision, exec="fused", cluster=c_,
+            prob = rnp.problem(cfg, precision=prec, exec="fused", cluster=c_,
                                threads=t_)
         else:
-            prob = rnp.problem(cfg, precision=args.precision, exec="fused", autotune=1)
+            prob = rnp.problem(cfg, precision=prec, exec="fused", autotune=1)
         u0 = torch.as_tensor(W.initial_condition(cfg)).to(dev)
         with rnp.Solver(prob, stream=stream) as solver:
             U0 = solver.coarse_sweep(0, u0)
@@ -553,7 +568,7 @@ def run_gpu(args):
             torch.cuda.synchronize(dev)
             torch.cuda.nvtx.range_pop()
             print(json.dumps({"profile": "done", "workload": describe(cfg),
-                              "precision": args.precision,
+                              "precision": prec,
                               "tiling": solver.stencil_config("fine")}))
         return 0
 
@@ -562,18 +577,20 @@ def run_gpu(args):
     extra = {}
     if rank == 0 and not args.skip_extra:
         if WORKLOAD == "bruss3d":
-            # BF16 tensor-core features on the same workload (8 x 256 new
-            # dataset rows per iteration), and the FP64 fine kernel's rate
+            # the other feature precision on the same workload, and the FP64
+            # fine kernel's rate (a full FP64 solve takes minutes)
+            other = "mixed" if res["precision"] == "mixed_bf16" else "mixed_bf16"
             extra.update(compare_forms(rnp, torch, WORKLOAD, cfg, args, stream, dev, u0, U,
-                                       [("mixed_bf16", "mixed_bf16", "fused")],
-                                       parareal=False))
+                                       [(other, other, "fused")], parareal=False,
+                                       timed=res["precision"]))
             extra["fp64_fused_fine_sample"] = fp64_fine_sample(rnp, torch, cfg, stream, dev,
                                                                u0)
         else:
             extra.update(compare_forms(rnp, torch, WORKLOAD, cfg, args, stream, dev, u0, U,
                                        [("fp64_plain", "fp64", "plain"),
                                         ("fp64_fused", "fp64", "fused"),
-                                        ("mixed_bf16", "mixed_bf16", "fused")]))
+                                        ("mixed_bf16", "mixed_bf16", "fused")],
+                                       timed=res["precision"]))
     solver.close()
     del U
     secondary = {}
@@ -583,11 +600,12 @@ def run_gpu(args):
                 continue
             r2, s2, u2, U2, cfg2 = measure(rnp, torch, name, args, rank, ws, None, dev,
                                            stream, flush, headline=False)
-            r2["config"] = line_config(name, args.precision, ws)
+            r2["config"] = line_config(name, r2["precision"], ws)
             r2.update(compare_forms(rnp, torch, name, cfg2, args, stream, dev, u2, U2,
                                     [("fp64_plain", "fp64", "plain"),
                                      ("fp64_fused", "fp64", "fused"),
-                                     ("mixed_bf16", "mixed_bf16", "fused")]))
+                                     ("mixed_bf16", "mixed_bf16", "fused")],
+                                    timed=r2["precision"]))
             s2.close()
             secondary[name] = r2
 
@@ -597,9 +615,9 @@ def run_gpu(args):
             "steps": res["steps"], "warmup": args.warmup,
             "ms_per_step": res["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+bf16+f64" if args.precision == "mixed_bf16" else "f32+f64",
+            "dtype": "f32+bf16+f64" if res["precision"] == "mixed_bf16" else "f32+f64",
             "data": "synthetic",
-            "config": line_config(WORKLOAD, args.precision, ws),
+            "config": line_config(WORKLOAD, res["precision"], ws),
         }
         for k in ("time_to_solution_ms", "K", "K_each", "fine_ms_per_iteration",
                   "fine_cell_updates_per_solve", "stencil_tiling", "sweep_ms", "fit_ms",
@@ -627,7 +645,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_bf16", "fp64"])
+    ap.add_argument("--precision", default=None, choices=["mixed", "mixed_bf16", "fp64"],
+                    help="timed form (default: the workload's, see TIMED_PRECISION)")
     ap.add_argument("--profile", action="store_true",
                     help="one untimed and one NVTX-ranged ('rnp_fine') fine step of the "
                          "timed form, for ncu; --batch / --slices reduce the launch")

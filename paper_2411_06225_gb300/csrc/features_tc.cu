@@ -90,28 +90,111 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
   return false;
 }
 
+// Stages K-block [kb, kb + kTcKB) of the S tile (rows r0.., FP32 -> BF16)
+// and of the A tile (neurons 0.., BF16) into the 128-byte-swizzled K-major
+// buffers sA / sB, zero-padded beyond R, M and d.
+//  * A: each 16-byte swizzle chunk (8 BF16) is copied global -> shared by
+//    cp.async without passing through registers (zero-filled beyond M);
+//    element copies where d does not allow 16-byte chunks.  The caller
+//    waits for the copies (tc_stage_wait) before the tile is used.
+//  * S: all of the thread's 16-byte loads (4 FP32 values each) are issued
+//    before any is converted, so they are in flight together; each becomes
+//    an 8-byte half chunk of BF16.  Element loads where the row start or d
+//    do not allow 16-byte loads.
+__device__ __forceinline__ void tc_stage(const float* S, Rows rows, int R,
+                                         const __nv_bfloat16* A, int M, long long d, int r0,
+                                         long long kb, unsigned char* sA, unsigned char* sB,
+                                         int tid) {
+  constexpr int kAPer = kTcN * (kTcKB / 8) / 128;   // 8 chunks per thread
+#pragma unroll
+  for (int i = 0; i < kAPer; ++i) {
+    const int e = tid + i * 128;
+    const int w = e >> 3, kk = (e & 7) * 8;
+    unsigned char* dst = sB + sw128_offset(w, kk);
+    if ((d & 7) == 0 && kb + kk + 8 <= d) {
+      const __nv_bfloat16* src = A + (long long)(w < M ? w : 0) * d + kb + kk;
+      const uint32_t n = w < M ? 16u : 0u;   // 0: zero fill
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)),
+                   "l"(src), "r"(n)
+                   : "memory");
+    } else {
+      __nv_bfloat16 t[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        t[j] = (w < M && kb + kk + j < d) ? A[(long long)w * d + kb + kk + j]
+                                          : __float2bfloat16(0.f);
+      *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(t);
+    }
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  constexpr int kSPer = kTcM * (kTcKB / 4) / 128;   // 16 groups of 4 per thread
+  float4 v[kSPer];
+#pragma unroll
+  for (int i = 0; i < kSPer; ++i) {
+    const int e = tid + i * 128;
+    const int r = e >> 4, kk = (e & 15) * 4;
+    const int row = r0 + r;
+    v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (row < R) {
+      const long long off = item_off(rows.off, rows.base, rows.stride, row);
+      const float* src = S + off + kb + kk;
+      if (((off | d) & 3) == 0 && kb + kk + 4 <= d) {
+        v[i] = *reinterpret_cast<const float4*>(src);
+      } else {
+        if (kb + kk + 0 < d) v[i].x = src[0];
+        if (kb + kk + 1 < d) v[i].y = src[1];
+        if (kb + kk + 2 < d) v[i].z = src[2];
+        if (kb + kk + 3 < d) v[i].w = src[3];
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < kSPer; ++i) {
+    const int e = tid + i * 128;
+    const int r = e >> 4, kk = (e & 15) * 4;
+    const __nv_bfloat162 lo = __floats2bfloat162_rn(v[i].x, v[i].y);
+    const __nv_bfloat162 hi = __floats2bfloat162_rn(v[i].z, v[i].w);
+    uint2 pk2;
+    pk2.x = *reinterpret_cast<const uint32_t*>(&lo);
+    pk2.y = *reinterpret_cast<const uint32_t*>(&hi);
+    *reinterpret_cast<uint2*>(sA + sw128_offset(r, kk)) = pk2;
+  }
+}
+
+// Waits for this thread's cp.async copies of the last staged tile.
+__device__ __forceinline__ void tc_stage_wait() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// One CTA: the 128-row x 128-neuron tile of rows r0.. over the K chunk
+// [k0, k0 + chunk).  Two operand stages: while the tensor core runs the MMAs
+// of K-block j (from stage j & 1), the threads load K-block j + 1 into the
+// other stage; a stage is refilled only after the commit of the MMAs that
+// read it (mbarrier j & 1, one phase per use).
 __global__ void __launch_bounds__(128, 1) k_feat_tc(const float* S, Rows rows, int R,
                                                     const __nv_bfloat16* A, int M, long long d,
-                                                    float* part, int nchunk, int* err) {
+                                                    int chunk_len, float* part, int nchunk,
+                                                    int* err) {
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
-  // 1024-byte aligned operand tiles: S tile (128 x 64 BF16) then A tile
+  // 1024-byte aligned operand stages: [stage][S tile 16 KB | A tile 16 KB]
   unsigned char* base = (unsigned char*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* sA = base;                       // 16 KB
-  unsigned char* sB = base + kTcM * kTcKB * 2;    // 16 KB
-  __shared__ __align__(8) uint64_t mbar;
+  constexpr int kStage = (kTcM + kTcN) * kTcKB * 2;   // 32 KB
+  __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
   __shared__ int aborted;
 
   const int tid = threadIdx.x, warp = tid >> 5;
   const int chunk = blockIdx.x;
   const int r0 = blockIdx.y * kTcM;
-  const long long k0 = (long long)chunk * kTcChunk;
-  const long long k1 = (k0 + kTcChunk) < d ? k0 + kTcChunk : d;
-  const uint32_t mbar_a = smem_u32(&mbar);
+  const long long k0 = (long long)chunk * chunk_len;
+  const long long k1 = (k0 + chunk_len) < d ? k0 + chunk_len : d;
+  const int nblk = (int)((k1 - k0 + kTcKB - 1) / kTcKB);
+  const uint32_t mb[2] = {smem_u32(&mbar[0]), smem_u32(&mbar[1])};
 
   if (tid == 0) {
     aborted = 0;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar_a) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb[0]) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb[1]) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -127,35 +210,17 @@ __global__ void __launch_bounds__(128, 1) k_feat_tc(const float* S, Rows rows, i
   const uint32_t tmem = tmem_base;
   constexpr uint32_t idesc = bf16_idesc(kTcM, kTcN);
 
-  uint32_t phase = 0;
-  int nblk = 0;
-  for (long long kb = k0; kb < k1; kb += kTcKB, ++nblk) {
-    // stage: S rows (FP32 -> BF16) and A rows (BF16), zero-padded
-    for (int e = tid; e < kTcM * (kTcKB / 2); e += blockDim.x) {
-      const int r = e / (kTcKB / 2), kk = (e % (kTcKB / 2)) * 2;
-      const int row = r0 + r;
-      float v0 = 0.f, v1 = 0.f;
-      if (row < R) {
-        const float* src = S + item_off(rows.off, rows.base, rows.stride, row);
-        if (kb + kk < d) v0 = src[kb + kk];
-        if (kb + kk + 1 < d) v1 = src[kb + kk + 1];
-      }
-      *reinterpret_cast<__nv_bfloat162*>(sA + sw128_offset(r, kk)) = __floats2bfloat162_rn(v0, v1);
-    }
-    for (int e = tid; e < kTcN * (kTcKB / 2); e += blockDim.x) {
-      const int w = e / (kTcKB / 2), kk = (e % (kTcKB / 2)) * 2;
-      __nv_bfloat162 v = __floats2bfloat162_rn(0.f, 0.f);
-      if (w < M) {
-        const __nv_bfloat16* src = A + (long long)w * d;
-        __nv_bfloat16 a0 = kb + kk < d ? src[kb + kk] : __float2bfloat16(0.f);
-        __nv_bfloat16 a1 = kb + kk + 1 < d ? src[kb + kk + 1] : __float2bfloat16(0.f);
-        v = __halves2bfloat162(a0, a1);
-      }
-      *reinterpret_cast<__nv_bfloat162*>(sB + sw128_offset(w, kk)) = v;
-    }
-    // make the generic-proxy writes visible to the tensor core (async proxy)
+  if (nblk > 0) tc_stage(S, rows, R, A, M, d, r0, k0, base, base + kTcM * kTcKB * 2, tid);
+  int done = 0;   // K-blocks whose MMAs are known complete
+  for (int j = 0; j < nblk; ++j) {
+    unsigned char* sA = base + (j & 1) * kStage;
+    unsigned char* sB = sA + kTcM * kTcKB * 2;
+    // make this thread's copies and generic-proxy writes of stage j & 1
+    // visible to the tensor core
+    tc_stage_wait();
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
+    if (aborted) break;
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint64_t da = sw128_desc(smem_u32(sA)), db = sw128_desc(smem_u32(sB));
@@ -164,7 +229,7 @@ __global__ void __launch_bounds__(128, 1) k_feat_tc(const float* S, Rows rows, i
         // advance 16 BF16 (32 B) along K inside the swizzled rows
         const uint64_t a = da + (uint64_t)((ks * 32) >> 4);
         const uint64_t b = db + (uint64_t)((ks * 32) >> 4);
-        const uint32_t acc = (nblk > 0 || ks > 0) ? 1u : 0u;
+        const uint32_t acc = (j > 0 || ks > 0) ? 1u : 0u;
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
@@ -173,22 +238,34 @@ __global__ void __launch_bounds__(128, 1) k_feat_tc(const float* S, Rows rows, i
       }
       asm volatile(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              mbar_a)
+              mb[j & 1])
           : "memory");
     }
-    // the staging buffers are reused: wait until these MMAs have read them
-    if (!mbar_wait(mbar_a, phase)) {
-      if (tid == 0) { atomicExch(err, 1); aborted = 1; }
+    if (j + 1 < nblk) {
+      // stage (j + 1) & 1 was last read by the MMAs of block j - 1
+      if (j >= 1) {
+        if (!mbar_wait(mb[(j + 1) & 1], (uint32_t)(((j - 1) >> 1) & 1))) {
+          if (tid == 0) { atomicExch(err, 1); aborted = 1; }
+        } else {
+          done = j;
+        }
+      }
+      __syncthreads();
+      if (aborted) break;
+      unsigned char* nA = base + ((j + 1) & 1) * kStage;
+      tc_stage(S, rows, R, A, M, d, r0, k0 + (long long)(j + 1) * kTcKB, nA,
+               nA + kTcM * kTcKB * 2, tid);
     }
-    __syncthreads();
-    if (aborted) {
-      // give the MMAs already issued one more bounded chance to finish before
-      // the tensor memory they write is released
-      mbar_wait(mbar_a, phase);
-      break;
-    }
-    phase ^= 1;
   }
+  // every MMA of this CTA complete (the commits of the last one or two
+  // blocks not yet waited for), bounded; on a timeout the accumulator is
+  // not read
+  for (int j = done; j < nblk; ++j)
+    if (!mbar_wait(mb[j & 1], (uint32_t)((j >> 1) & 1)) && tid == 0) {
+      atomicExch(err, 1);
+      aborted = 1;
+    }
+  __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (!aborted && nblk > 0) {
     // warp w owns tensor-memory lanes 32w .. 32w + 31 = tile rows
@@ -235,21 +312,32 @@ size_t features_tc_part_floats(int R, long long d) {
   return (size_t)R * features_tc_chunks(d) * kTcN;
 }
 
+// K-chunk length of one CTA: the longest multiple of kTcChunk (up to 8 x)
+// that still gives about two CTAs per SM over the row tiles, so that long
+// reductions pipeline their loads while small ones still fill the GPU.
+static int tc_chunk_len(int R, long long d) {
+  const long long tiles = (R + kTcM - 1) / kTcM;
+  int len = kTcChunk;
+  while (len < 8 * kTcChunk && tiles * ((d + 2 * len - 1) / (2 * len)) >= 2 * 152) len *= 2;
+  return len;
+}
+
 cudaError_t launch_features_tc(const __nv_bfloat16* A, const double* zeta, int M, long long d,
                                const float* S, Rows s_rows, int R, double* phi, Rows phi_rows,
                                float* part, int* err, cudaStream_t st) {
   if (R <= 0) return cudaSuccess;
   if (M > kTcN) return cudaErrorInvalidValue;
-  const int nch = features_tc_chunks(d);
-  // operand tiles need 33 KB; asking for 50 KB keeps at most four CTAs (4 x
-  // 128 tensor-memory columns = the SM's 512) resident per SM
-  const size_t smem = 50 * 1024;
+  const int len = tc_chunk_len(R, d);
+  const int nch = (int)((d + len - 1) / len);   // <= features_tc_chunks(d)
+  // two 32 KB operand stages plus alignment: at most three CTAs (3 x 128
+  // tensor-memory columns of the SM's 512) resident per SM
+  const size_t smem = 2 * (kTcM + kTcN) * kTcKB * 2 + 1024;
   cudaError_t e = cudaFuncSetAttribute((const void*)k_feat_tc,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid(nch, (R + kTcM - 1) / kTcM);
   count_launches(2);
-  k_feat_tc<<<grid, 128, smem, st>>>(S, s_rows, R, A, M, d, part, nch, err);
+  k_feat_tc<<<grid, 128, smem, st>>>(S, s_rows, R, A, M, d, len, part, nch, err);
   k_feat_tc_finish<<<(R * M + 255) / 256, 256, 0, st>>>(part, nch, R, M, zeta, phi, phi_rows);
   return cudaGetLastError();
 }

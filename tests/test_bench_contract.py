@@ -48,7 +48,8 @@ def test_reference_line(bench_mod, capsys, monkeypatch):
     assert line["config"]["grid"] == "40x40x40x2" and line["config"]["N"] == 256
     assert line["config"]["nF"] == 1000 and line["config"]["batch"] == 8
     assert "bruss3d" in line["config"]["workload"]
-    assert line["config"] == bench.line_config("bruss3d", "mixed", 1)
+    assert line["config"]["precision"] == "mixed_bf16"
+    assert line["config"] == bench.line_config("bruss3d", "mixed_bf16", 1)
 
 
 def test_reference_line_names_its_workload(bench_mod, capsys, monkeypatch):
@@ -61,6 +62,7 @@ def test_reference_line_names_its_workload(bench_mod, capsys, monkeypatch):
     assert line["config"]["grid"] == "100x50x3" and line["config"]["N"] == 235
     assert line["config"]["nF"] == 35 and "walls" in line["config"]["workload"]
     assert line["config"] == bench.line_config("swe_box", "mixed", 1)
+    assert bench.timed_precision("diffreact2d", None) == "mixed"
 
 
 def test_cpu_sample_keeps_the_slice_length():
