@@ -106,6 +106,9 @@ FLOPS_PER_CELL_UPDATE = {"diffreact2d": (4 * (16 + 12) + 2 * 13) / 2.0,
 STENCIL_TRAFFIC_PER_SLICE = {
     ("diffreact2d", (8, 256, 2, 4)): 16828416 / 64,
     ("diffreact2d", (16, 128, 2, 4)): 17310976 / 64,
+    # 16 slices of 40^3 x 2 (one member): 16,449,792 B read, 0 B written
+    # (the FP64 results stayed in L2 within the capture)
+    ("bruss3d", (10, 800, 2, 4)): 16449792 / 16,
 }
 
 
