@@ -525,6 +525,35 @@ def fp64_fine_sample(rnp, torch, cfg, stream, dev, u0):
                 "tiling": s.stencil_config("fine")}
 
 
+def serving_block(args) -> dict:
+    """C5: Poisson streams of shallow-water solves (grids {64^2, 128^2,
+    256^2} x 3, N in {32, 64, 128}, seeded Gaussian bumps) served with
+    continuous batching, at 0.3, 0.7 and 0.9 x the closed-loop throughput
+    measured first on the same request mix: p50 / p99 latency and solves/s.
+    `--serve-requests` requests per load (2000 is the full specification)."""
+    from paper_2411_06225_gb300 import serve
+    n = args.serve_requests
+    base = W.serving_stream(n, rate=1.0)
+    for r in base:
+        r["cfg"]["max_iters"] = min(12, r["cfg"]["N"])
+    closed = serve.run_stream([dict(r, arrival=0.0) for r in base[: max(16, n // 4)]],
+                              "mixed", 4)
+    rate = closed["solves_per_s"]
+    out = {"requests_per_load": n, "closed_loop_solves_per_s": rate,
+           "stream": "shallow water, grids {64,128,256}^2 x 3, N in {32,64,128}, "
+                     "Poisson arrivals, mixed precision, 4 slots per class pool, "
+                     "max_iters 12"}
+    for frac in (0.3, 0.7, 0.9):
+        reqs = W.serving_stream(n, rate=rate * frac)
+        for r in reqs:
+            r["cfg"]["max_iters"] = min(12, r["cfg"]["N"])
+        res = serve.run_stream(reqs, "mixed", 4)
+        out[f"{frac:.1f}x"] = {k: res[k] for k in ("p50_ms", "p99_ms", "mean_ms",
+                                                    "solves_per_s", "converged", "K_mean",
+                                                    "wall_s")}
+    return out
+
+
 def run_gpu(args):
     import torch
     import paper_2411_06225_gb300 as rnp
@@ -630,6 +659,11 @@ def run_gpu(args):
         line.update(extra)
         if secondary:
             line["workloads"] = secondary
+        if args.serve_requests > 0 and not args.skip_extra:
+            try:
+                line["serving"] = serving_block(args)
+            except Exception as e:  # report, do not fail the GPU line
+                line["serving"] = {"error": repr(e)[:200]}
         if not args.skip_cpu:
             try:
                 line["cpu_baseline"] = cpu_baseline(WORKLOAD)
@@ -662,6 +696,9 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=["bruss3d", "diffreact2d", "burgers1d", "bruss2d", "swe_box"])
     ap.add_argument("--max-iters", type=int, default=0)
+    ap.add_argument("--serve-requests", type=int, default=120,
+                    help="requests per load level of the serving streams (0: none; "
+                         "2000: the full specification)")
     ap.add_argument("--tile", default="",
                     help="fixed stencil tiling 'cluster,threads' instead of the autotuner's")
     args = ap.parse_args()
