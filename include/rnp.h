@@ -268,9 +268,10 @@ long long rnp_dim(const rnp_problem* prob);
  * the context's fine-step buffer as scratch: not during rnp_iterate.      */
 rnp_status rnp_features(rnp_ctx* ctx, const double* U, int R, double* phi);
 /* Stencil launch configuration in use: which = 0 fine step, 1 coarse step.
- * out[0] cluster size, out[1] threads per CTA, out[2] x-points per thread
- * (0 for the FP64 kernel), out[3] rows per thread, out[4] 1 if chosen by
- * timing.  Host out. */
+ * out (host, 6 ints): out[0] cluster size, out[1] threads per CTA, out[2]
+ * x-points per thread (0 for the FP64 kernel), out[3] rows per thread,
+ * out[4] 1 if chosen by timing, out[5] 1 if the step state lives in tensor
+ * memory (the wide FP32 kernel). */
 rnp_status rnp_stencil_config(const rnp_ctx* ctx, int which, int* out);
 
 /* --- allocation-free prediction (no counterpart in the paper) ----------- */

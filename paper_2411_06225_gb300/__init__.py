@@ -326,9 +326,10 @@ class Solver:
         self._check(lib().rnp_reset(self._ctx))
 
     def stencil_config(self, which: str = "fine") -> dict:
-        out = (C.c_int * 5)()
+        out = (C.c_int * 6)()
         self._check(lib().rnp_stencil_config(self._ctx, {"fine": 0, "coarse": 1}[which], out))
-        return dict(cluster=out[0], threads=out[1], px=out[2], rs=out[3], tuned=bool(out[4]))
+        return dict(cluster=out[0], threads=out[1], px=out[2], rs=out[3], tuned=bool(out[4]),
+                    tm=bool(out[5]))
 
     def pairs(self):
         out = (C.c_longlong * self.B)()

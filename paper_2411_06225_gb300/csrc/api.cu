@@ -786,6 +786,7 @@ rnp_status rnp_stencil_config(const rnp_ctx* c, int which, int* out) {
   out[2] = s.px;
   out[3] = s.px ? s.rs : s.R;
   out[4] = which == 0 ? c->tunedF : c->tunedG;
+  out[5] = s.px ? s.tm : 0;
   return RNP_OK;
 }
 

@@ -83,6 +83,7 @@ struct StencilCfg {
   int threads;   // threads per CTA
   int R;         // cells per thread (FP64 kernel)
   int px, rs;    // x-points and outer rows per thread (mixed kernel)
+  int tm;        // mixed kernel with the state in tensor memory (wide kernel)
 };
 
 Geom make_geom(const rnp_problem& p);

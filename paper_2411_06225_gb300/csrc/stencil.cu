@@ -211,15 +211,40 @@ static FusedFn mixed_fn_narrow(int kp, int PX, int RS, bool XS, bool WALL, bool 
   return nullptr;
 }
 
-// The mixed kernel for a block of `threads`: blocks above 512 threads run
-// the wide instantiation (72 registers per thread, state in tensor memory,
-// equal grid spacing only).
+// The mixed kernel: tm selects the wide instantiation (72 registers per
+// thread, state in tensor memory, equal grid spacing only, 128..800
+// threads), otherwise the 512-thread one.
 static FusedFn mixed_fn(const Geom& g, int PX, int RS, bool XS, bool WALL, bool RK,
-                        int threads) {
-  if (threads > 512)
-    return threads <= kWideThreads ? mixed_wide_fn(g.kp, PX, RS, XS, WALL, RK, g.iso)
-                                   : nullptr;
-  return mixed_fn_narrow(g.kp, PX, RS, XS, WALL, RK);
+                        int threads, bool tm) {
+  if (tm)
+    return threads >= kWideMinThreads && threads <= kWideThreads && threads % 32 == 0
+               ? mixed_wide_fn(g.kp, PX, RS, XS, WALL, RK, g.iso)
+               : nullptr;
+  return threads <= 512 ? mixed_fn_narrow(g.kp, PX, RS, XS, WALL, RK) : nullptr;
+}
+
+// Tensor-memory columns of a wide-kernel CTA: a power of two (>= 32) of at
+// least 3 RS ncomp PX columns (step state, accumulator, low words) per warp
+// times the warps that share a lane quadrant; 0 when the CTA may not take
+// them.  tcgen05.alloc waits while the SM's 512 columns are taken, and a
+// CTA waiting there inside a cluster can deadlock against another cluster
+// holding columns, so co-resident CTAs must never ask for more than 512.
+// Wide CTAs (72 registers per thread) claim at most their share of the
+// register file in columns (512 x threads x 72 / 65536), so any set of
+// them that fits an SM's registers fits its tensor memory; a CTA above 512
+// threads may take all 512 columns, because the registers it leaves
+// cannot hold another wide CTA (of at least 128 threads).  (The feature
+// map's 128 columns ride on its own 195-register threads: a feature CTA and
+// wide CTAs fitting one SM's registers stay within 512 columns too.)
+static int tm_columns(const Geom& g, int PX, int RS, int threads) {
+  const int nwq = ((threads / 32) + 3) / 4;
+  const int need = 3 * RS * g.ncomp * PX * nwq;
+  int cols = 32;
+  while (cols < need) cols *= 2;
+  if (cols > 512) return 0;
+  const bool alone = 65536 - threads * kWideRegs < kWideMinThreads * kWideRegs;
+  if (!alone && (long long)cols * 65536 > 512LL * threads * kWideRegs) return 0;
+  return cols;
 }
 
 static const int kRs[] = {1, 2, 4, 8, 16};
@@ -339,7 +364,8 @@ static bool launchable(FusedFn fn, int CS, int threads, size_t smem, int nitems)
 static thread_local int g_tile_relax = 0;  // 1: allow register tiles that spill a little
 
 static bool try_cfg(const Geom& g, bool fp32, int CS, int threads, int nitems,
-                    StencilCfg* out, int want_px = 0, int want_rs = 0, bool rk8 = false) {
+                    StencilCfg* out, int want_px = 0, int want_rs = 0, bool rk8 = false,
+                    int want_tm = -1) {
   if (g.outer % CS) return false;
   if (g.dims == 1 && CS != 1) return false;
   const long long nloc = g.outer / CS;
@@ -364,26 +390,35 @@ static bool try_cfg(const Geom& g, bool fp32, int CS, int threads, int nitems,
         if (RS * g.ncomp * PX > budget) continue;
         const long long t = tiles * (nloc / RS);
         if (t > kWideThreads || t < 1) continue;
-        // the wide kernel's tensor-memory accesses are warp-collective: whole
-        // warps only; its low words live in tensor memory
-        if (t > 512 && t % 32) continue;
-        const size_t smem = t > 512 ? smem_t : smem_n;
-        if (smem > (size_t)kMaxSmem) continue;
         if (threads > 0 && t != threads) continue;
-        // the RK4 and the Euler instantiation of this tile (the RK4 one is
-        // the larger: it decides launchability); blocks above 512 threads
-        // exist only as the wide kernel's tiles
-        FusedFn fn = mixed_fn(g, PX, RS, x_shuffles(g, PX), g.bc != 0, true, (int)t);
-        FusedFn fe = mixed_fn(g, PX, RS, x_shuffles(g, PX), g.bc != 0, false, (int)t);
-        if (!fn || !fe || !launchable(fn, CS, (int)t, smem, nitems) ||
-            !launchable(fe, CS, (int)t, smem, nitems))
-          continue;
-        out->cluster = CS;
-        out->threads = (int)t;
-        out->R = 0;
-        out->px = PX;
-        out->rs = RS;
-        return true;
+        // up to 512 threads the 512-thread kernel first (on the 2D
+        // workloads the autotuner measured it faster), then the wide kernel
+        // (state in tensor memory); above 512 threads only the wide kernel.
+        // The wide kernel's tensor-memory accesses are warp-collective
+        // (whole warps only) and its low words live in tensor memory (less
+        // shared memory)
+        for (int k = 0; k < 2; ++k) {
+          const int tm = t > 512 ? 1 - k : k;
+          if (want_tm >= 0 && tm != want_tm) continue;
+          const int cols = tm ? tm_columns(g, PX, RS, (int)t) : 0;
+          if (tm && cols == 0) continue;
+          const size_t smem = tm ? smem_t : smem_n;
+          if (smem > (size_t)kMaxSmem) continue;
+          // the RK4 and the Euler instantiation of this tile (the RK4 one
+          // is the larger: it decides launchability)
+          FusedFn fn = mixed_fn(g, PX, RS, x_shuffles(g, PX), g.bc != 0, true, (int)t, tm);
+          FusedFn fe = mixed_fn(g, PX, RS, x_shuffles(g, PX), g.bc != 0, false, (int)t, tm);
+          if (!fn || !fe || !launchable(fn, CS, (int)t, smem, nitems) ||
+              !launchable(fe, CS, (int)t, smem, nitems))
+            continue;
+          out->cluster = CS;
+          out->threads = (int)t;
+          out->R = 0;
+          out->px = PX;
+          out->rs = RS;
+          out->tm = tm;
+          return true;
+        }
       }
     }
     return false;
@@ -409,6 +444,7 @@ static bool try_cfg(const Geom& g, bool fp32, int CS, int threads, int nitems,
     out->threads = threads;
     out->R = R;
     out->px = out->rs = 0;
+    out->tm = 0;
     return true;
   }
   if (threads <= 0) {
@@ -427,6 +463,7 @@ static bool try_cfg(const Geom& g, bool fp32, int CS, int threads, int nitems,
   out->threads = threads;
   out->R = R;
   out->px = out->rs = 0;
+  out->tm = 0;
   return true;
 }
 
@@ -524,9 +561,12 @@ int list_stencil_cfgs(const Geom& g, bool fp32, int nitems, StencilCfg* out, int
             if (n >= maxn) break;
             if (g.nx % PX || (g.outer / CS) % RS) continue;
             const long long t = (g.plane / PX) * ((g.outer / CS) / RS);
-            StencilCfg c;
-            if (t >= 32 && t <= kWideThreads && try_cfg(g, true, CS, (int)t, nitems, &c, PX, RS))
-              out[n++] = c;
+            for (int tm = 1; tm >= 0 && n < maxn; --tm) {
+              StencilCfg c;
+              if (t >= 32 && t <= kWideThreads &&
+                  try_cfg(g, true, CS, (int)t, nitems, &c, PX, RS, false, tm))
+                out[n++] = c;
+            }
           }
       } else {
         StencilCfg c;
@@ -546,9 +586,10 @@ cudaError_t launch_stencil_fused(const Geom& g, const Coef& c, bool fp32, int sc
   if (it.n <= 0 || steps <= 0) return cudaSuccess;
   // a mixed-precision context uses the FP64 kernel where no FP32 tile fits
   const bool use_mixed = fp32 && cfg.px > 0;
+  const bool tm = use_mixed && cfg.tm;
   if (scheme == SCHEME_RK8 && use_mixed) return cudaErrorInvalidValue;  // FP64 only
   FusedFn fn = use_mixed ? mixed_fn(g, cfg.px, cfg.rs, x_shuffles(g, cfg.px), g.bc != 0,
-                                    scheme == SCHEME_RK4, cfg.threads)
+                                    scheme == SCHEME_RK4, cfg.threads, tm)
                : scheme == SCHEME_RK8 ? fused_rk8_fn(g.kp, cfg.R)
                                       : fused_fn(g.kp, cfg.R);
   if (!fn) return cudaErrorInvalidValue;
@@ -566,8 +607,9 @@ cudaError_t launch_stencil_fused(const Geom& g, const Coef& c, bool fp32, int sc
   P.nloc = g.outer / cfg.cluster;
   P.mcell = (P.nloc + 2) * (int)g.plane;
   P.mcl = P.nloc * (int)g.plane;
-  const bool tm = use_mixed && cfg.threads > 512;
   P.moff = use_mixed ? (int)mixed_tail_offset(g, cfg.cluster, tm) : 0;
+  P.tmcols = tm ? tm_columns(g, cfg.px, cfg.rs, cfg.threads) : 0;
+  if (tm && P.tmcols == 0) return cudaErrorInvalidValue;
   if (scheme == SCHEME_RK8) rk8_tableau(P.rk);
   else memset(P.rk, 0, sizeof(P.rk));
   cudaLaunchConfig_t lc = {};

@@ -155,6 +155,7 @@ struct FusedParams {
   // parameter space instead of being kept in registers
   int nloc, mcell, mcl;
   int moff;          // byte offset of the mbarriers in the dynamic shared memory
+  int tmcols;        // tensor-memory columns the CTA allocates (wide kernel)
   // eighth-order fine solver (FP64 kernel): a_{s,j} at rk[s*(s-1)/2 + j] for
   // stages s = 1..10, j < s, then b_0..b_10 at rk[55..65]
   double rk[66];
@@ -1239,15 +1240,18 @@ __device__ __forceinline__ void mixed_body(const FusedParams& P) {
         if constexpr (TM) acc[r][q][p] = (float)(v - (double)h);   // staged for TMEM
         else ulo[q * ncl + o * plane + rowoff + p] = (float)(v - (double)h);
       }
-  // TM: 512 TMEM columns for the CTA (at most 8 warps share a lane
-  // quadrant, each using 3 RS NC PX <= 48 columns: step state, accumulator,
-  // low words), allocated by warp 0; the allocation writes the base address
-  // to tm_base
+  // TM: P.tmcols TMEM columns for the CTA (a power of two of at least
+  // 3 RS NC PX columns per warp times the warps sharing a lane quadrant:
+  // step state, accumulator, low words), allocated by warp 0; the
+  // allocation writes the base address to tm_base.  The host sizes the
+  // columns so that the CTAs that can share an SM never ask for more than
+  // its 512 (an allocation that had to wait could deadlock two clusters).
   volatile uint32_t* const tm_base = reinterpret_cast<volatile uint32_t*>(stop_in + 2);
   if constexpr (TM) {
     if (threadIdx.x < 32) {
-      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
-                       cta_smem_u32(const_cast<uint32_t*>(tm_base)))
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       cta_smem_u32(const_cast<uint32_t*>(tm_base))),
+                   "r"((uint32_t)P.tmcols)
                    : "memory");
       asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -1428,7 +1432,8 @@ __device__ __forceinline__ void mixed_body(const FusedParams& P) {
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (threadIdx.x < 32)
-      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(*tm_base)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tm_base),
+                   "r"((uint32_t)P.tmcols)
                    : "memory");
   }
   double* out = P.out + item_off(P.it.dst_off, P.it.dst_base, P.it.dst_stride, item) + base;
@@ -1456,14 +1461,17 @@ __global__ void __launch_bounds__(512, 1) k_stencil_mixed(const __grid_constant_
 // Registers per thread of the wide kernel.  The register file is split
 // evenly over the SM's four schedulers (16384 each) and a block's warps are
 // dealt out among them, so 25 warps put 7 on one scheduler: 7 x 32 x 72 =
-// 16128 registers fit, 80 would not.  Blocks of up to 800 threads launch.
+// 16128 registers fit, 80 would not.  Blocks of 128 to 800 threads launch
+// (above 512 threads one block per SM; at 256 threads three).
 static constexpr int kWideRegs = 72;
 static constexpr int kWideThreads = 800;
+static constexpr int kWideMinThreads = 128;
 
-// The wide kernel keeps the step state and the accumulator in tensor memory
-// (TM), which leaves the registers to the stencil's working rows, and
-// requires equal grid spacing on every axis (ISO: a cheaper Laplacian with
-// fewer constants); the host falls back to the other kernel otherwise.
+// The wide kernel keeps the step state, the accumulator and the low words in
+// tensor memory (TM), which leaves the registers to the stencil's working
+// rows, and requires equal grid spacing on every axis (ISO: a cheaper
+// Laplacian with fewer constants); the host falls back to the other kernel
+// otherwise.
 template <int KP, int PX, int RS, bool XS, bool WALL, bool RK>
 __global__ void __maxnreg__(kWideRegs) k_stencil_mixed_wide(const __grid_constant__ FusedParams P) {
   mixed_body<KP, PX, RS, XS, WALL, RK, true, true>(P);
@@ -1549,8 +1557,9 @@ inline FusedFn mixed_wide_for(int PX, int RS) {
   if (PX == 4 && RS == 2) return k_stencil_mixed_wide<KP, 4, 2, false, false, RK>;
   return nullptr;
 }
-// defined in stencil_wide.cu: the 3D Brusselator's wide kernels on grids of
-// equal spacing (nullptr for other operators, tiles and grids)
+// defined in stencil_wide.cu: the wide kernels of the reaction-diffusion
+// operators on grids of equal spacing (nullptr for other operators, tiles
+// and grids)
 FusedFn mixed_wide_fn(int kp, int PX, int RS, bool XS, bool WALL, bool RK, bool iso);
 
 // Per-PDE entry points, defined in stencil_<pde>.cu.
