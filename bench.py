@@ -104,8 +104,8 @@ FLOPS_PER_CELL_UPDATE = {"diffreact2d": (4 * (16 + 12) + 2 * 13) / 2.0,
 # traffic grows in proportion to the slices; a tiling with no capture
 # reports null.
 STENCIL_TRAFFIC_PER_SLICE = {
-    ("diffreact2d", (8, 256, 2, 4)): 16828416 / 64,
-    ("diffreact2d", (16, 128, 2, 4)): 17310976 / 64,
+    # 64 slices of 128^2 x 2: 16,840,192 B read, 0 B written
+    ("diffreact2d", (8, 256, 2, 4)): 16840192 / 64,
     # 16 slices of 40^3 x 2 (one member): 16,449,792 B read, 0 B written
     # (the FP64 results stayed in L2 within the capture)
     ("bruss3d", (10, 800, 2, 4)): 16449792 / 16,
