@@ -20,7 +20,13 @@ solve, correction and norm.  The 2D diffusion-reaction workload (128^2 x 2,
 N = 64, F = RK4 x 2000, G = Euler x 8) is measured after it and reported
 under "workloads", in its own timed form (FP32 features on CUDA cores: BF16
 features cost it one more iteration), with the plain FP64 GPU form, the
-fused FP64 form, BF16 features and classic Parareal beside it.
+fused FP64 form, BF16 features and classic Parareal beside it; so are the
+2D Brusselator (256^2 x 2, N = 128), the paper's shallow-water dam break
+(100 x 50 x 3 with walls, N = 235, beside its plain FP64 form) and the 1D
+Burgers workload (d = 128, N = 16, all FP64 as specified).  Under
+"serving": Poisson streams of shallow-water solves served with continuous
+batching at 0.3, 0.7 and 0.9 x the measured closed-loop throughput (p50 /
+p99 latency, solves/s).
 
 value = fine cell-updates per second over the whole job (sum over ranks of
 the fine RK4 unknown-steps the solves performed / max over ranks of the
@@ -59,15 +65,27 @@ import numpy as np  # noqa: E402
 import workloads as W  # noqa: E402
 
 WORKLOAD = "bruss3d"  # the headline workload; --workload measures the others
-SECONDARY = ("diffreact2d",)
+# Workloads measured after the headline (reported under "workloads"), with
+# the other forms timed beside each: every form on the 2D diffusion-reaction
+# workload; the plain FP64 form on the paper's dam break; none where a full
+# FP64 solve takes minutes (2D Brusselator) or the timed form is FP64.
+SECONDARY = {
+    "diffreact2d": (("fp64_plain", "fp64", "plain"), ("fp64_fused", "fp64", "fused"),
+                    ("mixed_bf16", "mixed_bf16", "fused")),
+    "bruss2d": (),
+    "swe_box": (("fp64_plain", "fp64", "plain"),),
+    "burgers1d": (),
+}
 METRIC = ("Parareal time-to-solution @tol 1e-6 vs plain FP64; cell-updates/s, %HBM; "
           "p50/p99")
 UNIT = "cell-updates/s"
 
 # Timed form per workload: BF16 random features where they leave the
 # iteration count unchanged and save time (3D Brusselator: K = 3 either way),
-# FP32 features elsewhere (diffusion-reaction: K = 5 with BF16, 4 without).
-TIMED_PRECISION = {"bruss3d": "mixed_bf16"}
+# FP32 features elsewhere (diffusion-reaction: K = 5 with BF16, 4 without);
+# the 1D Burgers workload is specified all-FP64 (its coarse step is unstable
+# in FP32 rounding).
+TIMED_PRECISION = {"bruss3d": "mixed_bf16", "burgers1d": "fp64"}
 
 # Workload settings of the benchmark beyond the canonical configurations:
 # the 3D Brusselator's dataset arena is sized for 16 iterations (8 members x
@@ -79,8 +97,12 @@ BENCH_OVERRIDES = {"bruss3d": dict(max_iters=16)}
 #   bytes: the FP32 state read and written once per step, 8 B per unknown,
 #          against the measured HBM copy bandwidth;
 #   flops: FP32 flops per cell-step, against the FP32 ALU peak.
+#   fp64flops: FP64 flops per cell-step (the all-FP64 Burgers workload),
+#          against the nominal FP64 rate (no measured FP64 peak is given).
 ROOF_UNIT = {"bruss3d": ("bytes", 8.0), "bruss2d": ("bytes", 8.0),
-             "swe_box": ("bytes", 8.0), "diffreact2d": ("flops", 40.0)}
+             "swe_box": ("bytes", 8.0), "diffreact2d": ("flops", 40.0),
+             "burgers1d": ("fp64flops", 60.0)}
+FP64_NOMINAL_TFLOPS = 1.25
 
 # Every FP32 multiply and add of the fine step counted separately, per
 # cell-update, from the right-hand side formulas, plus 13 per unknown for
@@ -324,13 +346,19 @@ def roofline(name: str, cells_per_launch: float, launch_s: float, tf: dict,
              "unit": "GB/s", "frac": ach / pk["hbm_gbs"], "traffic": traffic,
              "per_unit": f"{per:g} B per cell-step (FP32 state read + written once)",
              "peak_source": "hbm_gbs of the measured peaks (copy bandwidth)"}
+    elif kind == "fp64flops":
+        ach = cells_per_launch * per / launch_s / 1e12
+        r = {"kernel": kname, "bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS,
+             "unit": "TFLOP/s", "frac": ach / FP64_NOMINAL_TFLOPS, "traffic": traffic,
+             "per_unit": f"{per:g} FP64 flop per cell-step",
+             "peak_source": "nominal FP64 rate of the GB300 (no measured FP64 peak)"}
     else:
         ach = cells_per_launch * per / launch_s / 1e12
         r = {"kernel": kname, "bound": "alu", "achieved": ach, "peak": alu_peak,
              "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": traffic,
              "per_unit": f"{per:g} FP32 flop per cell-step", "peak_source": alu_src}
     # the same launch counted with every FP32 operation of the step
-    fl = FLOPS_PER_CELL_UPDATE.get(name)
+    fl = FLOPS_PER_CELL_UPDATE.get(name) if tf["px"] else None
     if fl:
         a2 = cells_per_launch * fl / launch_s / 1e12
         r["alu_recount"] = {"flop_per_cell_step": fl, "achieved": a2, "peak": alu_peak,
@@ -627,19 +655,21 @@ def run_gpu(args):
     del U
     secondary = {}
     if rank == 0 and not args.skip_extra:
-        for name in SECONDARY:
+        for name, forms in SECONDARY.items():
             if name == WORKLOAD:
                 continue
-            r2, s2, u2, U2, cfg2 = measure(rnp, torch, name, args, rank, ws, None, dev,
-                                           stream, flush, headline=False)
-            r2["config"] = line_config(name, r2["precision"], ws)
-            r2.update(compare_forms(rnp, torch, name, cfg2, args, stream, dev, u2, U2,
-                                    [("fp64_plain", "fp64", "plain"),
-                                     ("fp64_fused", "fp64", "fused"),
-                                     ("mixed_bf16", "mixed_bf16", "fused")],
-                                    timed=r2["precision"]))
-            s2.close()
-            secondary[name] = r2
+            try:
+                r2, s2, u2, U2, cfg2 = measure(rnp, torch, name, args, rank, ws, None, dev,
+                                               stream, flush, headline=False)
+                r2["config"] = line_config(name, r2["precision"], ws)
+                r2.update(compare_forms(rnp, torch, name, cfg2, args, stream, dev, u2, U2,
+                                        list(forms), parareal=name == "diffreact2d",
+                                        timed=r2["precision"]))
+                s2.close()
+                del U2
+                secondary[name] = r2
+            except Exception as e:  # report, do not fail the GPU line
+                secondary[name] = {"error": repr(e)[:200]}
 
     if rank == 0:
         line = {
