@@ -216,10 +216,17 @@ rnp_status rnp_randnet_predict(rnp_ctx* ctx, const double* q, double* out);
 /* Full RandNet-Parareal solve (Alg. 1 with Eq. 3, Eq. 5, Eq. randnet or
  * Eq. 4).  Resets the dataset and scaling, then iterates until every state
  * passed Eq. 5 or max_iters.
- *   u0 : device [B][d];  U : device [B][N+1][d] receives U_0 .. U_N.
+ *   u0 : [B][d];  U : [B][N+1][d] receives U_0 .. U_N.  Each of u0 and U
+ *        may be device memory or HOST memory (pinned or pageable; told
+ *        apart with cudaPointerGetAttributes).  With U in host memory the
+ *        states U_0 .. U_L of a member, final once Eq. 5 has set L, are
+ *        copied out after every iteration on a copy stream of the context,
+ *        overlapping the next iteration; the remaining states at the end
+ *        (into pinned memory by a copy kernel through its device address).
  *   stats : host, may be NULL.
  * Returns RNP_OK, or RNP_ENOTCONV with U holding the last iterate.
- * Blocks until the result is on the device.                               */
+ * Blocks until the result is in U (also on an error: no copy into U is
+ * still in flight when the call returns).                                 */
 rnp_status rnp_solve(rnp_ctx* ctx, const double* u0, double* U, rnp_stats* stats);
 
 /* Message of the last failed call on ctx ("" if none).  ctx may be NULL

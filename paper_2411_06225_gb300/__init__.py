@@ -174,10 +174,12 @@ def dim(p: Problem) -> int:
     return lib().rnp_dim(C.byref(p))
 
 
-def _ptr(t, dtype=None, shape=None, name="tensor"):
+def _ptr(t, dtype=None, shape=None, name="tensor", host_ok=False):
+    """Address of a contiguous FP64 tensor: a CUDA tensor, or also a CPU
+    tensor (host memory, pinned or not) where the call takes host memory."""
     import torch
-    if not isinstance(t, torch.Tensor) or not t.is_cuda:
-        raise TypeError(f"{name} must be a CUDA tensor")
+    if not isinstance(t, torch.Tensor) or not (t.is_cuda or (host_ok and t.device.type == "cpu")):
+        raise TypeError(f"{name} must be a CUDA tensor" + (" or a CPU tensor" if host_ok else ""))
     if t.dtype != torch.float64:
         raise TypeError(f"{name} must be float64")
     if not t.is_contiguous():
@@ -258,12 +260,15 @@ class Solver:
         return out
 
     def solve(self, u0, U=None, check: bool = True):
-        """Returns (U [B, N+1, d], stats dict).  With check=False an
-        RNP_ENOTCONV result is returned instead of raised."""
+        """Returns (U [B, N+1, d], stats dict).  u0 and U may be CUDA or CPU
+        tensors (host memory: the library copies in and out, the output
+        while later iterations run); U defaults to a new CUDA tensor.  With
+        check=False an RNP_ENOTCONV result is returned instead of raised."""
         U = self._empty(self.B, self.N + 1, self.d) if U is None else U
         st = Stats()
-        rc = lib().rnp_solve(self._ctx, _ptr(u0, shape=(self.B, self.d)),
-                             _ptr(U, shape=(self.B, self.N + 1, self.d)), C.byref(st))
+        rc = lib().rnp_solve(self._ctx, _ptr(u0, shape=(self.B, self.d), host_ok=True),
+                             _ptr(U, shape=(self.B, self.N + 1, self.d), host_ok=True),
+                             C.byref(st))
         if rc == RNP_ENOTCONV and not check:
             return U, st.as_dict(self.B)
         self._check(rc)

@@ -84,6 +84,10 @@ struct rnp_ctx {
   // CUDA graphs of the solve's sweep keyed by its first index
   cudaStream_t st2 = nullptr;
   cudaEvent_t evf = nullptr, evj = nullptr;
+  // copy stream and its event: a solve into host memory sends each member's
+  // converged states out while the next iteration computes
+  cudaStream_t st3 = nullptr;
+  cudaEvent_t evc = nullptr;
   std::vector<cudaGraphExec_t> sweep_graph;
   std::vector<long long> sweep_graph_launches;
   std::string msg;
@@ -250,6 +254,8 @@ void destroy_buffers(rnp_ctx* c) {
   for (auto& g : c->sweep_graph)
     if (g) cudaGraphExecDestroy(g);
   if (c->st2) cudaStreamDestroy(c->st2);
+  if (c->evc) cudaEventDestroy(c->evc);
+  if (c->st3) cudaStreamDestroy(c->st3);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
   if (c->st) cudaStreamDestroy(c->st);
@@ -662,6 +668,8 @@ rnp_status rnp_create(const rnp_problem* prob, void* cuda_stream, rnp_ctx** out)
   ok &= cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking) == cudaSuccess;
   ok &= cudaEventCreateWithFlags(&c->evf, cudaEventDisableTiming) == cudaSuccess;
   ok &= cudaEventCreateWithFlags(&c->evj, cudaEventDisableTiming) == cudaSuccess;
+  ok &= cudaStreamCreateWithFlags(&c->st3, cudaStreamNonBlocking) == cudaSuccess;
+  ok &= cudaEventCreateWithFlags(&c->evc, cudaEventDisableTiming) == cudaSuccess;
   c->sweep_graph.assign(N + 2, nullptr);
   c->sweep_graph_launches.assign(N + 2, 0);
   if (!ok) {
@@ -701,6 +709,7 @@ rnp_status rnp_destroy(rnp_ctx* c) {
   DevGuard gd(c->dev);
   if (c->st) cudaStreamSynchronize(c->st);
   if (c->st2) cudaStreamSynchronize(c->st2);
+  if (c->st3) cudaStreamSynchronize(c->st3);
   destroy_buffers(c);
   delete c;
   return RNP_OK;
@@ -947,9 +956,9 @@ rnp_status rnp_coarse_sweep(rnp_ctx* c, int first, const double* U_first, double
 namespace {
 
 // k = 0 of Alg. 1 for the members with want[b]: U_b,0 = u0 (row b of u0,
-// member stride u0_bstride), U_b,i = G(U_b,i-1) for i = 1..N with the G values
-// kept for the first targets, then the member's scaling.  The members become
-// active with an empty dataset.
+// member stride u0_bstride; device or host memory), U_b,i = G(U_b,i-1) for
+// i = 1..N with the G values kept for the first targets, then the member's
+// scaling.  The members become active with an empty dataset.
 rnp_status start_members(rnp_ctx* c, const std::vector<int>& want, const double* u0,
                          long long u0_bstride, rnp_stats* st) {
   const int B = c->B, N = c->N;
@@ -966,7 +975,7 @@ rnp_status start_members(rnp_ctx* c, const std::vector<int>& want, const double*
   for (int b = 0; b < B; ++b)
     if (want[b])
       CK(cudaMemcpyAsync(c->U + (long long)b * sb, u0 + (long long)b * u0_bstride,
-                         sizeof(double) * d, cudaMemcpyDeviceToDevice, c->st));
+                         sizeof(double) * d, cudaMemcpyDefault, c->st));
   CK(cudaEventRecord(c->ev[0], c->st));
   for (int i = 1; i <= N; ++i) {
     Items it = affine(B, (long long)(i - 1) * d, sb, (long long)i * d, sb, c->d_mask);
@@ -993,6 +1002,54 @@ rnp_status start_members(rnp_ctx* c, const std::vector<int>& want, const double*
     }
   return RNP_OK;
 }
+
+// Where a buffer lives: host memory (pinned, or pageable and unknown to
+// CUDA), and for pinned memory its device address (null if it has none).
+struct HostMem {
+  bool host = false;
+  double* dptr = nullptr;
+};
+HostMem host_memory(void* p) {
+  HostMem h;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    h.host = true;
+    return h;
+  }
+  h.host = a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
+  if (a.type == cudaMemoryTypeHost) h.dptr = static_cast<double*>(a.devicePointer);
+  return h;
+}
+
+// Sends states sent[b] + 1 .. upto[b] of every member from the context's U
+// to Uout (member stride (N + 1) d) on the copy stream, after the work on
+// the main stream so far.  States U_0 .. U_L of a member are final once
+// Eq. 5 has set L: later iterations only read them.
+rnp_status send_states(rnp_ctx* c, double* Uout, std::vector<int>& sent,
+                       const std::vector<int>& upto) {
+  const long long d = c->d, sb = (long long)(c->N + 1) * d;
+  bool any = false;
+  for (int b = 0; b < c->B; ++b) any |= upto[b] > sent[b];
+  if (!any) return RNP_OK;
+  CK(cudaEventRecord(c->evc, c->st));
+  CK(cudaStreamWaitEvent(c->st3, c->evc, 0));
+  for (int b = 0; b < c->B; ++b) {
+    if (upto[b] <= sent[b]) continue;
+    const long long off = (long long)b * sb + (long long)(sent[b] + 1) * d;
+    CK(cudaMemcpyAsync(Uout + off, c->U + off,
+                       sizeof(double) * d * (upto[b] - sent[b]), cudaMemcpyDefault, c->st3));
+    sent[b] = upto[b];
+  }
+  return RNP_OK;
+}
+
+// Waits for the copy stream when a solve into host memory leaves, also on
+// an error, so that no copy into the caller's buffer outlives the call.
+struct CopyDrain {
+  rnp_ctx* c;
+  ~CopyDrain() { cudaStreamSynchronize(c->st3); }
+};
 
 // One iteration of Alg. 1 for every active member: the parallel fine step
 // over all their unconverged starts (one launch), the dataset append of
@@ -1152,14 +1209,42 @@ rnp_status rnp_solve(rnp_ctx* c, const double* u0, double* Uout, rnp_stats* stat
   memset(&st, 0, sizeof(st));
   rnp_status s;
   const std::vector<int> all(B, 1);
+  // U in host memory: each member's converged states go out on the copy
+  // stream after every iteration, overlapping the next one; the rest at the
+  // end, into pinned memory by SM stores through its device address (after
+  // the iterations the destination's address translations are cold, and the
+  // copy engine resolves them a few at a time: 2.1 GB took 240 ms that way
+  // and 57 ms by SM stores on GB300; 11 ms either way when warm)
+  const HostMem out = host_memory(Uout);
+  const bool host_out = out.host;
+  CopyDrain drain{c};
+  std::vector<int> sent(B, -1);
   s = start_members(c, all, u0, d, &st);
   if (s != RNP_OK) return s;
   int n_active = B;
   while (n_active > 0) {
     s = iterate_once(c, &st, &n_active);
     if (s != RNP_OK) return s;
+    if (host_out && n_active > 0 && (s = send_states(c, Uout, sent, c->mL))) return s;
   }
-  CK(cudaMemcpyAsync(Uout, c->U, sizeof(double) * B * sb, cudaMemcpyDeviceToDevice, c->st));
+  if (host_out && out.dptr) {
+    Segments sg;
+    sg.n = 0;
+    for (int b = 0; b < B; ++b) {
+      if (sent[b] >= N) continue;
+      sg.off[sg.n] = (long long)b * sb + (long long)(sent[b] + 1) * d;
+      sg.len[sg.n] = (long long)(N - sent[b]) * d;
+      ++sg.n;
+      sent[b] = N;
+    }
+    CK(launch_copy_segments(c->U, out.dptr, sg, c->st));
+    CK(cudaStreamSynchronize(c->st3));
+  } else if (host_out) {
+    if ((s = send_states(c, Uout, sent, std::vector<int>(B, N)))) return s;
+    CK(cudaStreamSynchronize(c->st3));
+  } else {
+    CK(cudaMemcpyAsync(Uout, c->U, sizeof(double) * B * sb, cudaMemcpyDeviceToDevice, c->st));
+  }
   CK(cudaStreamSynchronize(c->st));
   st.converged = 1;
   st.L = N;

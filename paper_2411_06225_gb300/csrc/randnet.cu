@@ -1107,4 +1107,30 @@ cudaError_t launch_copy_rows(const double* src, const long long* src_off, double
   return cudaGetLastError();
 }
 
+// Segment s: dst[off[s] .. off[s] + len[s]) = src[same range].  Used to
+// write states into pinned host memory through its device address: SM
+// stores keep many address translations of the destination in flight at
+// once, where the copy engine takes them a few at a time.
+__global__ void k_copy_segments(const double* __restrict__ src, double* __restrict__ dst,
+                                Segments sg) {
+  const int s = blockIdx.y;
+  const long long off = sg.off[s], len = sg.len[s];
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < len;
+       j += (long long)gridDim.x * blockDim.x)
+    dst[off + j] = src[off + j];
+}
+
+cudaError_t launch_copy_segments(const double* src, double* dst, const Segments& sg,
+                                 cudaStream_t st) {
+  if (sg.n <= 0) return cudaSuccess;
+  long long lmax = 0;
+  for (int s = 0; s < sg.n; ++s) lmax = sg.len[s] > lmax ? sg.len[s] : lmax;
+  if (lmax <= 0) return cudaSuccess;
+  // about 16 blocks of 512 threads per SM over all segments
+  const int bx = grid_cap(lmax, 512, (152 * 16 + sg.n - 1) / sg.n);
+  count_launches(1);
+  k_copy_segments<<<dim3(bx, sg.n), 512, 0, st>>>(src, dst, sg);
+  return cudaGetLastError();
+}
+
 }  // namespace rnp

@@ -267,4 +267,15 @@ cudaError_t launch_copy_rows(const double* src, const long long* src_off,
                              double* dst, const long long* dst_off, long long d,
                              int rows, cudaStream_t st);
 
+// Up to RNP_MAX_BATCH segments [off, off + len) (in doubles) copied from src
+// to dst at the same offsets; dst may be the device address of pinned host
+// memory.
+struct Segments {
+  long long off[RNP_MAX_BATCH];
+  long long len[RNP_MAX_BATCH];
+  int n;
+};
+cudaError_t launch_copy_segments(const double* src, double* dst, const Segments& sg,
+                                 cudaStream_t st);
+
 }  // namespace rnp
