@@ -741,11 +741,11 @@ __device__ __forceinline__ void st_shared_vec(uint32_t addr, const float* v) {
 }
 
 // Sends PX values (element `elem` of the row, counted in floats from the
-// start of the buffer) of outer row 0 (to_prev) or nloc - 1.
+// start of the buffer) of outer row 0 (to_prev) or nloc - 1; t is the
+// CTA's target table (*h.tab), read once by the caller for all its pushes.
 template <int PX>
-__device__ __forceinline__ void push_edge(const HaloOut& h, bool to_prev, uint32_t elem,
-                                          const float* v) {
-  const uint4 t = *h.tab;
+__device__ __forceinline__ void push_edge(const HaloOut& h, const uint4& t, bool to_prev,
+                                          uint32_t elem, const float* v) {
   const uint32_t a = (to_prev ? t.x : t.y) + h.boff + 4u * elem;
   const uint32_t mb = to_prev ? t.z : t.w;  // 0: a local target (wall)
   if (h.self || mb == 0) st_shared_vec<PX>(a, v);
@@ -755,21 +755,20 @@ __device__ __forceinline__ void push_edge(const HaloOut& h, bool to_prev, uint32
 // push_edge for component q; a shallow-water wall ghost row (a local target
 // when WALL) mirrors the row with its normal momentum hv negated
 template <int KP, int PX, bool WALL>
-__device__ __forceinline__ void push_edge_q(const HaloOut& h, bool to_prev, uint32_t elem,
-                                            const float* v, int q) {
+__device__ __forceinline__ void push_edge_q(const HaloOut& h, const uint4& t, bool to_prev,
+                                            uint32_t elem, const float* v, int q) {
   if constexpr (WALL && KP == KP_SWE) {
     if (q == 2) {
-      const uint4 t = *h.tab;
       if (h.self || (to_prev ? t.z : t.w) == 0) {
         float nv[PX];
 #pragma unroll
         for (int p = 0; p < PX; ++p) nv[p] = -v[p];
-        push_edge<PX>(h, to_prev, elem, nv);
+        push_edge<PX>(h, t, to_prev, elem, nv);
         return;
       }
     }
   }
-  push_edge<PX>(h, to_prev, elem, v);
+  push_edge<PX>(h, t, to_prev, elem, v);
 }
 
 // --- tensor memory as per-thread storage -------------------------------
@@ -996,11 +995,13 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
           kq[0] = fma2(pk1(kk[iD]), lq[0], sub2(sub2(sub2(a, a3), pk1(kk[2])), b));
           kq[1] = fma2(pk1(kk[iD + 1]), lq[1], sub2(a, b));
         } else {
-          // D0 lap u + (a - (1 + b) u + v u^2);  D1 lap v + (b u - v u^2)
+          // D0 lap u + (a - (1 + b) u + v u^2);  D1 lap v + (b u - v u^2),
+          // factored: a + u (v u - (1 + b)) and u (b - v u), where
+          // b - v u = (b - (1 + b)) - (v u - (1 + b))
           constexpr int iD = ISO ? kIsoD : 2;
-          const float2 ba2 = mul2(b, mul2(a, a));
-          kq[0] = fma2(pk1(kk[iD]), lq[0], add2(fma2(pk1(-kk[4]), a, pk1(kk[0])), ba2));
-          kq[1] = fma2(pk1(kk[iD + 1]), lq[1], fma2(pk1(kk[1]), a, mul2(pk1(-1.f), ba2)));
+          const float2 s0 = fma2(b, a, pk1(-kk[4]));
+          kq[0] = fma2(pk1(kk[iD]), lq[0], fma2(a, s0, pk1(kk[0])));
+          kq[1] = fma2(pk1(kk[iD + 1]), lq[1], mul2(a, sub2(pk1(kk[1] - kk[4]), s0)));
         }
 #pragma unroll
         for (int q = 0; q < NC; ++q) {
@@ -1091,18 +1092,25 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
       }
     }
 #pragma unroll
-    for (int q = 0; q < NC; ++q) {
-      st_vec<PX>(pBn + q * ncell, wout[q]);
-      if (DIMS >= 2) {
-        // edge rows are visited first: row 0 (walking up) or nloc - 1 (down);
-        // a CTA with a single row group also sends its last row at r = RS - 1
-        if (r == 0 && ho.on && ho.edge)
-          push_edge_q<KP, PX, WALL>(ho, ho.first, q * ncell + rowoff, wout[q], q);
-        if (r == RS - 1 && ho.on && ho.first && ho.last)
-          push_edge_q<KP, PX, WALL>(ho, false, q * ncell + rowoff, wout[q], q);
+    for (int q = 0; q < NC; ++q) st_vec<PX>(pBn + q * ncell, wout[q]);
+    if (DIMS >= 2) {
+      // edge rows are visited first: row 0 (walking up) or nloc - 1 (down);
+      // a CTA with a single row group also sends its last row at r = RS - 1
+      // (one test per row for all components)
+      const bool e0 = r == 0 && ho.on && ho.edge;
+      const bool e1 = r == RS - 1 && ho.on && ho.first && ho.last;
+      if (e0 || e1) {
+        const uint4 t = *ho.tab;
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+          if (e0) push_edge_q<KP, PX, WALL>(ho, t, ho.first, q * ncell + rowoff, wout[q], q);
+          if (e1) push_edge_q<KP, PX, WALL>(ho, t, false, q * ncell + rowoff, wout[q], q);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < NC; ++q)
 #pragma unroll
         for (int p = 0; p < PX; ++p) { back[q][p] = cur[q][p]; cur[q][p] = ahead[q][p]; }
-      }
     }
     pB += rstep;
     pBn += rstep;
@@ -1279,6 +1287,7 @@ __device__ __forceinline__ void mixed_body(const FusedParams& P) {
   // stage 0's halo: the initial edge rows
   if (DIMS >= 2) {
     const HaloOut h0 = halo_out(0, true);
+    const uint4 t0 = *h0.tab;
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
       // outer rows 0 and nloc - 1 sit in register rows 0 / RS - 1 or, walking
@@ -1289,8 +1298,8 @@ __device__ __forceinline__ void mixed_body(const FusedParams& P) {
         v0[p] = dir > 0 ? uh[0][q][p] : uh[RS - 1][q][p];
         v1[p] = dir > 0 ? uh[RS - 1][q][p] : uh[0][q][p];
       }
-      if (first) push_edge_q<KP, PX, WALL>(h0, true, q * ncell + rowoff, v0, q);
-      if (last) push_edge_q<KP, PX, WALL>(h0, false, q * ncell + rowoff, v1, q);
+      if (first) push_edge_q<KP, PX, WALL>(h0, t0, true, q * ncell + rowoff, v0, q);
+      if (last) push_edge_q<KP, PX, WALL>(h0, t0, false, q * ncell + rowoff, v1, q);
     }
   }
 
