@@ -819,6 +819,13 @@ __device__ __forceinline__ void tm_wait_ld(float* v) {
 #pragma unroll
   for (int i = 0; i < N; ++i) asm volatile("" : "+f"(v[i]));
 }
+// The same register fence for more loaded registers after a tm_wait_ld (one
+// wait covers every earlier load of the thread).
+template <int N>
+__device__ __forceinline__ void tm_fence_ld(float* v) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) asm volatile("" : "+f"(v[i]));
+}
 __device__ __forceinline__ void tm_wait_st() {
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
@@ -881,16 +888,15 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
     // and written in Euler steps and the last RK stage)
     float ur[NC][PX], ar[NC][PX], lr[NC][PX];
     if constexpr (TM) {
+      // the row's loads in flight together, then one wait
       tm_ld<NC * PX>(tm + (uint32_t)(r * NC * PX), &ur[0][0]);
-      if (!euler && STAGE > 0) {
+      if (!euler && STAGE > 0)
         tm_ld<NC * PX>(tm + (uint32_t)((RS + r) * NC * PX), &ar[0][0]);
-        tm_wait_ld<NC * PX>(&ar[0][0]);
-      }
-      if (euler || STAGE == 3) {
+      if (euler || STAGE == 3)
         tm_ld<NC * PX>(tm + (uint32_t)((2 * RS + r) * NC * PX), &lr[0][0]);
-        tm_wait_ld<NC * PX>(&lr[0][0]);
-      }
       tm_wait_ld<NC * PX>(&ur[0][0]);
+      if (!euler && STAGE > 0) tm_fence_ld<NC * PX>(&ar[0][0]);
+      if (euler || STAGE == 3) tm_fence_ld<NC * PX>(&lr[0][0]);
     }
     float (&U_)[NC][PX] = TM ? ur : uh[r];
     float (&A_)[NC][PX] = TM ? ar : acc[r];
@@ -989,10 +995,11 @@ __device__ __forceinline__ void mixed_stage(const FusedParams& P, const float* _
         }
         const float2 a = Cq[0], b = Cq[1];
         if constexpr (KP == KP_DIFFREACT) {
-          // Du lap u + (u - u^3 - c - v);  Dv lap v + (u - v)
-          const float2 a3 = mul2(mul2(a, a), a);
+          // Du lap u + (u - u^3 - c - v);  Dv lap v + (u - v), the first
+          // reaction term factored as -c - (u (u^2 - 1) + v)
           constexpr int iD = ISO ? kIsoD : 0;
-          kq[0] = fma2(pk1(kk[iD]), lq[0], sub2(sub2(sub2(a, a3), pk1(kk[2])), b));
+          const float2 w = fma2(a, fma2(a, a, pk1(-1.f)), b);
+          kq[0] = fma2(pk1(kk[iD]), lq[0], sub2(pk1(-kk[2]), w));
           kq[1] = fma2(pk1(kk[iD + 1]), lq[1], sub2(a, b));
         } else {
           // D0 lap u + (a - (1 + b) u + v u^2);  D1 lap v + (b u - v u^2),
@@ -1437,7 +1444,7 @@ __device__ __forceinline__ void mixed_body(const FusedParams& P) {
       tm_ld<NC * PX>(tm + (uint32_t)(r * NC * PX), &uh[r][0][0]);
       tm_ld<NC * PX>(tm + (uint32_t)((2 * RS + r) * NC * PX), &acc[r][0][0]);  // low words
       tm_wait_ld<NC * PX>(&uh[r][0][0]);
-      tm_wait_ld<NC * PX>(&acc[r][0][0]);
+      tm_fence_ld<NC * PX>(&acc[r][0][0]);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
