@@ -921,6 +921,12 @@ __device__ __forceinline__ void block_max_to(unsigned long long* dst, unsigned l
   }
 }
 
+// FAST (mixed-precision contexts, whose next query is kept in FP32 only):
+// the correction by fused multiply-adds and the scaled query by the
+// reciprocal of the range; otherwise every operation rounded separately, as
+// the oracle's Eq. 3 update and scaling do.  (GB300's FP64 pipe makes the
+// separate operations and the division the kernel's cost.)
+template <bool FAST>
 __global__ void __launch_bounds__(256) k_update(const double* g, long long g_bstride,
                                                 const double* Y, long long cap, long long d,
                                                 const double* alpha, const int* idx,
@@ -933,10 +939,13 @@ __global__ void __launch_bounds__(256) k_update(const double* g, long long g_bst
   const int me = meff[b];
   __shared__ double a[RNP_MAX_M];
   __shared__ const double* Yl[RNP_MAX_M];
+  __shared__ double rinv[3];
   if (threadIdx.x < me) {
     a[threadIdx.x] = alpha[b * RNP_MAX_M + threadIdx.x];
     Yl[threadIdx.x] = Y + ((long long)b * cap + idx[b * RNP_MAX_M + threadIdx.x]) * d;
   }
+  if (FAST && qo.q32 && threadIdx.x >= 32 && threadIdx.x < 35)
+    rinv[threadIdx.x - 32] = 1.0 / qo.r[b * 3 + threadIdx.x - 32];
   __syncthreads();
   const double* gb = g ? g + (long long)b * g_bstride : nullptr;
   double* ob = out + (long long)b * out_bstride;
@@ -945,7 +954,11 @@ __global__ void __launch_bounds__(256) k_update(const double* g, long long g_bst
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < d;
        j += (long long)gridDim.x * blockDim.x) {
     double acc = 0.0;
-    for (int l = 0; l < me; ++l) acc = __dadd_rn(acc, __dmul_rn(a[l], Yl[l][j]));
+    if constexpr (FAST) {
+      for (int l = 0; l < me; ++l) acc = fma(a[l], Yl[l][j], acc);
+    } else {
+      for (int l = 0; l < me; ++l) acc = __dadd_rn(acc, __dmul_rn(a[l], Yl[l][j]));
+    }
     const double v = gb ? __dadd_rn(gb[j], acc) : acc;
     if (err) {
       const unsigned long long e = (unsigned long long)__double_as_longlong(fabs(v - ob[j]));
@@ -954,11 +967,16 @@ __global__ void __launch_bounds__(256) k_update(const double* g, long long g_bst
     bad |= !isfinite(v);
     ob[j] = v;
     if (qo.q64 || qo.q32) {
-      // the next step's scaled query, as k_scale_rows computes it
-      const int q = (int)(j / qo.n);
-      const double sv = __ddiv_rn(__dsub_rn(v, qo.c[b * 3 + q]), qo.r[b * 3 + q]);
-      if (qo.q64) qo.q64[(long long)b * d + j] = sv;
-      if (qo.q32) qo.q32[(long long)b * d + j] = (float)sv;
+      // the next step's scaled query, as k_scale_rows computes it (FAST:
+      // times the reciprocal); component q of at most three
+      const int q = j >= qo.n ? (j >= 2 * qo.n ? 2 : 1) : 0;
+      if constexpr (FAST) {
+        qo.q32[(long long)b * d + j] = (float)(__dsub_rn(v, qo.c[b * 3 + q]) * rinv[q]);
+      } else {
+        const double sv = __ddiv_rn(__dsub_rn(v, qo.c[b * 3 + q]), qo.r[b * 3 + q]);
+        if (qo.q64) qo.q64[(long long)b * d + j] = sv;
+        if (qo.q32) qo.q32[(long long)b * d + j] = (float)sv;
+      }
     }
   }
   if (bad) atomicExch(nonfinite, 1);
@@ -1006,9 +1024,14 @@ cudaError_t launch_update(const double* g, long long g_bstride, const double* Y,
                           unsigned long long* err, long long err_bstride, int* nonfinite,
                           int B, const int* gate, cudaStream_t st, QueryOut qo) {
   count_launches(1);
-  k_update<<<update_grid(d, B), 256, 0, st>>>(g, g_bstride, Y, cap, d, alpha, idx, meff, out,
-                                              out_bstride, err, err_bstride, nonfinite, gate,
-                                              qo);
+  if (qo.q32 && !qo.q64)
+    k_update<true><<<update_grid(d, B), 256, 0, st>>>(g, g_bstride, Y, cap, d, alpha, idx, meff,
+                                                      out, out_bstride, err, err_bstride,
+                                                      nonfinite, gate, qo);
+  else
+    k_update<false><<<update_grid(d, B), 256, 0, st>>>(g, g_bstride, Y, cap, d, alpha, idx, meff,
+                                                       out, out_bstride, err, err_bstride,
+                                                       nonfinite, gate, qo);
   return cudaGetLastError();
 }
 
