@@ -5,7 +5,9 @@ precision against the FP64 oracle.
 
 Bounds: features within 1e-4 of the largest feature magnitude (FP32
 accumulation of d <= 32768 products); the solve within 1e-5 relative of the
-FP64 oracle with K within 1."""
+FP64 oracle with K within 1.  With M > 128 neurons the rows take the CUDA-core
+kernel of the sweep's single queries (also with few rows, and d = 1250 not a
+multiple of the 1024-element chunks)."""
 import numpy as np
 import pytest
 
@@ -37,7 +39,7 @@ def bf16(a):
 
 
 @pytest.mark.parametrize("nx,M,rows", [(64, 100, 64), (64, 100, 37), (128, 128, 64),
-                                        (40, 150, 20)])
+                                        (40, 150, 20), (25, 150, 3), (25, 150, 19)])
 def test_feature_map_on_tensor_cores(R, nx, M, rows):
     cfg = W.config("diffreact2d", nx=nx, ny=nx, M=M)
     d = W.dim(cfg)
