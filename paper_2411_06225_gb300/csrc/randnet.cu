@@ -324,20 +324,24 @@ __host__ __device__ inline long long nn_chunk_len(long long d) {
 int nn_chunks(long long d) { return (int)((d + nn_chunk_len(d) - 1) / nn_chunk_len(d)); }
 
 // Chunking of the distance sums for P stored rows: nn_chunks(d) chunks of
-// nn_chunk_len(d) while P x chunks stays within kNnTasks warp tasks; beyond,
-// fewer and longer chunks (about kNnTasks tasks, never more chunks than
+// nn_chunk_len(d) while P x chunks stays within the task budget; beyond,
+// fewer and longer chunks (about that many tasks, never more chunks than
 // nn_chunks(d)), so the selection kernel finishes fewer partials per row.
-// The partial and the selection kernels both derive it from (d, P).
+// The budget is kNnTasks warp tasks per member, half that for states of
+// 65536 unknowns or more (the scan then streams from HBM, and longer tasks
+// keep more of it in flight per warp).  The partial and the selection
+// kernels both derive the chunking from (d, P).
 static constexpr int kNnTasks = 8192;
 __host__ __device__ inline void nn_split(long long d, int P, long long* chl, int* nch) {
   const long long c0 = nn_chunk_len(d);
   const int n0 = (int)((d + c0 - 1) / c0);
-  if ((long long)P * n0 <= kNnTasks) {
+  const int tasks = d >= 65536 ? kNnTasks / 2 : kNnTasks;
+  if ((long long)P * n0 <= tasks) {
     *chl = c0;
     *nch = n0;
     return;
   }
-  const int want = P < kNnTasks ? kNnTasks / P : 1;
+  const int want = P < tasks ? tasks / P : 1;
   long long c = (d + want - 1) / want;
   c = ((c + 255) / 256) * 256;
   *chl = c;
