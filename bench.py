@@ -131,9 +131,12 @@ FLOPS_PER_CELL_UPDATE = {"diffreact2d": (4 * (16 + 12) + 2 * 13) / 2.0,
 STENCIL_TRAFFIC_PER_SLICE = {
     # 64 slices of 128^2 x 2: 16,840,192 B read, 0 B written
     ("diffreact2d", (8, 256, 2, 4)): 16840192 / 64,
-    # 16 slices of 40^3 x 2 (one member): 16,449,792 B read, 0 B written
+    # the same launch at the 16-CTA clusters of 128 threads: 16,838,144 B
+    # read, 0 B written
+    ("diffreact2d", (16, 128, 2, 4)): 16838144 / 64,
+    # 16 slices of 40^3 x 2 (one member): 16,448,512 B read, 0 B written
     # (the FP64 results stayed in L2 within the capture)
-    ("bruss3d", (10, 800, 2, 4)): 16449792 / 16,
+    ("bruss3d", (10, 800, 2, 4)): 16448512 / 16,
 }
 
 

@@ -1,7 +1,9 @@
 """The reference arm of bench.py on CPU: one JSON line with the contract's
 keys, the oracle's figures as its value, and its e2e object; other ranks
 print nothing.  The timed oracle sample is replaced by a stub so the test
-takes milliseconds (the sample itself is the oracle, tested elsewhere)."""
+takes milliseconds (the sample itself is the oracle, tested elsewhere).
+Also the roofline arithmetic of the GPU line: each workload's fine launch
+in the unit its roof is stated in, the measured traffic scaled by slices."""
 import argparse
 import json
 
@@ -123,3 +125,42 @@ def test_dam_break_workload_recipe():
     inside = (phi(15.0) - phi(-5.0)) * (phi(7.0) - phi(-3.0))
     assert abs((h - 1.0).sum() * 0.1 * 0.1 - inside) < 1e-4   # midpoint rule, h = 0.1
     assert "walls" in bench.describe(cfg) and "F=RK4x35" in bench.describe(cfg)
+
+
+PK = {"hbm_gbs": 6662.6, "sm_max_mhz": 2070.0}
+WIDE = {"cluster": 10, "threads": 800, "px": 2, "rs": 4}
+
+
+def test_roofline_of_the_headline_in_bytes_per_cell_step():
+    """The 3D Brusselator's fine launch against HBM in the workload's unit,
+    8 B per cell-step, and against the FP32 ALU with every operation counted."""
+    import bench
+    cells, launch_s, slices = 2.518e11, 1.3407, 1967.0
+    r = bench.roofline("bruss3d", cells, launch_s, WIDE, slices, PK)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and "_wide" in r["kernel"]
+    assert r["achieved"] == pytest.approx(cells * 8 / launch_s / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6662.6)
+    assert r["traffic"] == pytest.approx(16448512 / 16 * slices)
+    alu = 152 * 128 * 2 * 2070e6 / 1e12
+    assert r["alu_recount"]["flop_per_cell_step"] == (4 * (21 + 18) + 2 * 13) / 2.0
+    assert r["alu_recount"]["frac"] == pytest.approx(cells * 91 / launch_s / 1e12 / alu)
+
+
+def test_roofline_of_the_other_workloads_in_their_units():
+    """Diffusion-reaction against the FP32 ALU at 40 flop per cell-step,
+    Burgers (all FP64) against the nominal FP64 rate at 60 flop."""
+    import bench
+    tf = {"cluster": 16, "threads": 128, "px": 2, "rs": 4}
+    r = bench.roofline("diffreact2d", 1e11, 0.5, tf, 64, PK)
+    alu = 152 * 128 * 2 * 2070e6 / 1e12
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert r["frac"] == pytest.approx(1e11 * 40 / 0.5 / 1e12 / alu)
+    assert r["traffic"] == pytest.approx(16838144.0)
+    fp64 = {"cluster": 1, "threads": 64, "px": 0, "rs": 0, "R": 2}
+    r = bench.roofline("burgers1d", 1e9, 0.5, fp64, 16, PK)
+    assert r["bound"] == "alu" and r["peak"] == 1.25
+    assert r["frac"] == pytest.approx(1e9 * 60 / 0.5 / 1e12 / 1.25)
+    assert "alu_recount" not in r and r["traffic"] is None
+    # a tiling without a capture reports no traffic
+    r = bench.roofline("bruss3d", 1e11, 1.0, dict(WIDE, cluster=8, rs=5), 100, PK)
+    assert r["traffic"] is None
