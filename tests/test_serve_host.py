@@ -118,3 +118,26 @@ def test_the_number_of_pools_is_capped(server):
     assert len(server.pools) == 1
     assert all(p.closed for p in server.created[:-1])
     assert len(server.created) >= len(keys)
+
+
+def test_request_stream_is_seeded_poisson_over_the_stated_mix():
+    """The C5 request stream: the same seed gives the same stream, arrivals
+    increase with exponential gaps of mean 1 / rate, grid sides and slice
+    counts come from the stated sets (each drawn), every request its own
+    seeded bump of the shallow-water system."""
+    a = W.serving_stream(2000, rate=4.0)
+    b = W.serving_stream(2000, rate=4.0)
+    assert [(r["arrival"], r["cfg"]["seed"]) for r in a] == [(r["arrival"], r["cfg"]["seed"]) for r in b]
+    t = np.array([r["arrival"] for r in a])
+    gaps = np.diff(np.concatenate([[0.0], t]))
+    assert (gaps > 0).all()
+    # mean of 2000 exponential gaps: 1/4 within 5 standard errors
+    assert abs(gaps.mean() - 0.25) < 5 * 0.25 / np.sqrt(2000)
+    # exponential: the coefficient of variation is 1
+    assert abs(gaps.std() / gaps.mean() - 1.0) < 0.1
+    grids = {r["cfg"]["nx"] for r in a}
+    slices = {r["cfg"]["N"] for r in a}
+    assert grids == {64, 128, 256} and slices == {32, 64, 128}
+    assert all(r["cfg"]["nx"] == r["cfg"]["ny"] and r["cfg"]["pde"] == "swe2d" for r in a)
+    assert len({r["cfg"]["seed"] for r in a}) > 1990
+    assert W.serving_stream(50, rate=4.0, seed=1)[0]["arrival"] != a[0]["arrival"]
